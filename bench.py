@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-dendrogram and effective pair-distance rate of exact NNM single
+linkage on one GB300, through the C ABI.
+
+A step is one pass of the whole path on resident synthetic data: nnm_create (checks,
+centring, operand layout), nnm_cluster (all-pairs candidate sweep, exact binary64
+re-rank, merge rounds, edge sort, restriction walk, labels) and nnm_destroy.
+value = N(N-1)/2 / time-to-dendrogram, in G pair-distances/s (all ranks summed).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp16|fp32]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G pair-distances/s and time-to-dendrogram at N=2M,d=25 (BF16+FP64-rerank vs FP32)"
+UNIT = "Gpairs/s"
+DEFAULT_WORKLOAD = "nnm_n2097152_d25"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--n", type=int, default=None, help="override N (smaller runs)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--compare", default="", help="comma list of other precisions timed for one step each")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------
+# distributed plumbing: replicas only (the method's partition is not sharded here)
+# ------------------------------------------------------------------------------------
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (cpu_baseline and --impl reference)
+# ------------------------------------------------------------------------------------
+
+def oracle_pair_rate(X, seconds, seed=0):
+    """Exact binary64 1-NN of sampled rows against all rows with the oracle, every core.
+    Returns (Gpairs/s, rows sampled, seconds, cores)."""
+    import oracle
+    oracle.build()
+    N = X.shape[0]
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(N, size=min(16, N), replace=False)
+    t0 = time.perf_counter()
+    oracle.knn(X, 1, queries=rows)
+    t1 = time.perf_counter() - t0
+    R = int(min(max(16, 16 * seconds / max(t1, 1e-3)), N))
+    rows = rng.choice(N, size=R, replace=False)
+    t0 = time.perf_counter()
+    oracle.knn(X, 1, queries=rows)
+    dt = time.perf_counter() - t0
+    return R * (N - 1) / dt / 1e9, R, dt, os.cpu_count()
+
+
+def run_reference(args, world, rank):
+    from paper_1402_3789_gb300.inputs import make
+    if rank != 0:
+        return
+    X = make(args.workload, n=args.n)
+    N, d = X.shape
+    per_step = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    rates = []
+    for s in range(args.warmup + args.steps):
+        rate, R, dt, cores = oracle_pair_rate(X, per_step, seed=s)
+        if s >= args.warmup:
+            rates.append((rate, R, dt))
+    value = statistics.median(r for r, _, _ in rates)
+    R = rates[-1][1]
+    ms = statistics.mean(dt for _, _, dt in rates) * 1e3
+    sample = (f"exact binary64 1-NN of {R} sampled rows against all {N} rows per step (oracle, all cores); "
+              f"a full oracle dendrogram evaluates N(N-1)/2 pairs at this per-pair rate")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "d": d, "sample_rows": R},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------
+# our path
+# ------------------------------------------------------------------------------------
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1402_3789_gb300 import nnm
+    from paper_1402_3789_gb300.inputs import WORKLOADS, make
+
+    nnm.load_library()
+    w = WORKLOADS[args.workload]
+    X = make(args.workload, n=args.n)
+    N, d = X.shape
+    restr = dict(w.restrictions)
+    Xd = torch.from_numpy(X).cuda()
+    stream = torch.cuda.current_stream()
+
+    def step(precision):
+        ctx = nnm.nnm_create(Xd, precision=precision)
+        try:
+            res = nnm.nnm_cluster(ctx, restr)
+            st = nnm.nnm_get_stats(ctx)
+            st["ms_prep"] = st["ms_prep"]
+            return st, res
+        finally:
+            nnm.nnm_destroy(ctx)
+
+    for _ in range(args.warmup):
+        step(args.precision)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    last = None
+    for _ in range(args.steps):
+        st, last = step(args.precision)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    elapsed_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    ms_per_step = elapsed_ms / args.steps
+    pairs = N * (N - 1) / 2
+    value = world * pairs / (ms_per_step / 1e3) / 1e9
+
+    # roofline of the dominant kernel: the all-pairs candidate sweep
+    peaks, peak_kind = load_peaks()
+    sweep_ms = statistics.mean(s["sweep_ms_per_launch_full"] for s in stats)
+    sweep_pairs = stats[-1]["full_sweep_pairs"]
+    if args.precision == "fp32":
+        flops = sweep_pairs * 3 * d
+        # FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops (FMA) x clock under load
+        clk = (clocks.get("sm_mhz") or 1447.0) * 1e6
+        peak = 152 * 128 * 2 * clk / 1e12
+        roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock sampled"}
+    else:
+        kpad = stats[-1]["k_pad"]
+        flops = sweep_pairs * 2 * kpad
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)   # same rate for fp16 operands
+        roof = {"bound": "tensor", "peak_source": f"bf16_tflops_sustained ({peak_kind})"}
+    achieved = flops / (sweep_ms / 1e3) / 1e12
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                 "kernel": "k_sweep_tc" if args.precision != "fp32" else "k_sweep_fp32",
+                 "algorithmic_flops_per_launch": flops, "launch_ms": sweep_ms})
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16": "bf16+f64", "fp16": "f16+f64", "fp32": "f32+f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": args.workload, "N": N, "d": d, "precision": args.precision,
+                       "restrictions": restr, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (X and operands > 129 MB)" if N * d * 4 > 129e6
+                       else "inputs smaller than L2"},
+            "time_to_dendrogram_ms": ms_per_step,
+            "phases_ms": {k: statistics.mean(s[k] for s in stats) for k in
+                          ("ms_prep", "ms_sweep", "ms_rerank", "ms_rounds", "ms_sort", "ms_restrict", "ms_labels")},
+            "rounds": stats[-1]["rounds"], "rows_rescanned": stats[-1]["rows_rescanned"],
+            "rows_overflowed": stats[-1]["rows_overflowed"], "rerank_pairs": stats[-1]["rerank_pairs"],
+            "max_candidates_per_row": stats[-1]["max_candidates"],
+            "max_abs_err_vs_fp64": max(s["max_abs_err"] for s in stats),
+            "max_rel_err_vs_fp64": max(s["max_rel_err"] for s in stats),
+            "n_merges": last.n_merges, "n_clusters": last.n_clusters,
+            "kernel_rate_gpairs": stats[-1]["pairs_evaluated"] / 2 / (statistics.mean(s["ms_sweep"] for s in stats) / 1e3) / 1e9,
+            "roofline": roof, "clocks": clocks,
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
+
+    # the other precisions named by --compare, one step each
+    comp = {}
+    for p in [c for c in args.compare.split(",") if c and c != args.precision]:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        st, _ = step(p)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        comp[p] = {"time_to_dendrogram_ms": ms, "value": pairs / (ms / 1e3) / 1e9, "sweep_ms_full": st["sweep_ms_per_launch_full"],
+                   "rounds": st["rounds"], "rows_rescanned": st["rows_rescanned"]}
+    if comp:
+        line["compare"] = comp
+
+    # end to end through the public API from host memory
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        nm = 0
+        for _ in range(args.steps):
+            merges, labels, K = nnm.cluster_host(X, restr, precision=args.precision)
+            nm = merges.shape[0]
+        t1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(t0.elapsed_time(t1), world) / args.steps
+        line["e2e"] = {"value": world * pairs / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": N * d * 4, "d2h_bytes_per_step": N * 4 + nm * 32, "ms_per_step": e2e_ms}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, R, dt, cores = oracle_pair_rate(X, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"exact binary64 1-NN of {R} sampled rows against all {N} rows "
+                                          f"({dt:.1f} s); a full oracle dendrogram evaluates N(N-1)/2 pairs "
+                                          f"at this per-pair rate"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

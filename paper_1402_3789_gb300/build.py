@@ -1,0 +1,90 @@
+"""Build ``libnnm.so`` (the sm_103a CUDA library behind include/nnm.h) in-tree.
+
+Every ``csrc/*.cu`` translation unit is compiled by nvcc in parallel for
+``compute_103a``/``sm_103a`` only, then linked into
+``paper_1402_3789_gb300/_build/libnnm.so``.  Cross-compiling needs no GPU.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+# translation units: (output name, source, extra defines)
+UNITS = [
+    ("nnm_api", "nnm_api.cu", []),
+    ("prep", "prep.cu", []),
+    ("sweep_fp32_lo", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_LO"]),
+    ("sweep_fp32_hi", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_HI"]),
+    ("sweep_tc", "sweep_tc.cu", []),
+    ("rerank", "rerank.cu", []),
+    ("rounds", "rounds.cu", []),
+    ("sort", "sort.cu", []),
+    ("restrict", "restrict.cu", []),
+]
+
+
+def nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def library_path() -> str:
+    return os.path.join(BUILD, "libnnm.so")
+
+
+def _sources_mtime() -> float:
+    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    paths.append(os.path.join(ROOT, "include", "nnm.h"))
+    paths.append(os.path.abspath(__file__))
+    return max(os.path.getmtime(p) for p in paths)
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    out = library_path()
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= _sources_mtime():
+        return out
+    os.makedirs(BUILD, exist_ok=True)
+    cc = nvcc()
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+                     "-I", CSRC]
+    if ptxas_info:
+        common += ["-Xptxas", "-v"]
+
+    def compile_unit(unit):
+        name, src, defs = unit
+        obj = os.path.join(BUILD, name + ".o")
+        cmd = [cc] + common + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+        return obj, r.stderr
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(compile_unit, UNITS))
+    if verbose or ptxas_info:
+        for _, err in results:
+            if err:
+                sys.stderr.write(err)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-rpath=/usr/local/cuda/lib64",
+                         "-o", tmp] + [o for o, _ in results]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, out)
+    return out
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv))

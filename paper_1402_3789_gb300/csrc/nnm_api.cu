@@ -1,0 +1,794 @@
+// nnm_api.cu -- the C ABI (include/nnm.h) and the host-side driver of the device path.
+//
+// The paper's main module validates the data and runs the managers that keep the GPU
+// busy ("Objectives of the main module", "Tasks of the first/second level manager").
+// Here one host thread enqueues every step on the caller's stream; all arithmetic runs
+// in this library's kernels:
+//   nnm_create   K0 checks + operand preparation
+//   nnm_nearest  K1/K2 candidate sweep -> K3 exact re-rank (-> collect pass)
+//   nnm_cluster  round 0: cached exact k nearest neighbours of every row; merge rounds
+//                (K4 component minima, masked rescans, K5 hooking + pointer jumping);
+//                K6 edge sort; K7 restriction walk; K8 labels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "nnm_internal.cuh"
+
+using namespace nnm;
+
+#include <atomic>
+
+namespace nnm {
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace nnm
+
+struct nnm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    const float *X = nullptr;
+    int64_t N = 0;
+    int d = 0;
+    nnm_precision prec = NNM_PREC_FP32;
+    nnm_options opt{};
+    int64_t Npad = 0;
+    int dp = 0;
+    int kpad = 0;
+    int fp16 = 0;
+    double scale = 1.0;
+    Margin margin{};
+    // operands
+    float *Xs = nullptr;
+    uint16_t *XA = nullptr, *XB = nullptr;
+    float *r = nullptr, *P = nullptr, *E = nullptr;
+    // sweep / re-rank scratch
+    float *cand_v = nullptr;
+    uint32_t *cand_j = nullptr;
+    size_t cand_cap = 0;         // entries
+    uint32_t *ovf_row = nullptr;
+    float *ovf_thr = nullptr;
+    size_t ovf_cap = 0;          // slots
+    uint32_t *coll_cnt = nullptr, *coll_j = nullptr;
+    double *coll_D = nullptr;
+    size_t coll_cap = 0;         // entries
+    // cache and rounds
+    int kc = 0;
+    uint32_t *cache_j = nullptr;
+    double *cache_D = nullptr;
+    uint8_t *cache_n = nullptr, *cache_exh = nullptr;
+    uint32_t *comp = nullptr, *parent = nullptr, *list = nullptr;
+    unsigned long long *row_D = nullptr, *row_ab = nullptr, *best_D = nullptr, *best_ab = nullptr;
+    uint8_t *row_state = nullptr, *frozen = nullptr;
+    nnm_edge *edges = nullptr, *edges_tmp = nullptr, *tree = nullptr;
+    int64_t n_tree = 0;
+    // restriction walk / labels
+    uint32_t *uf_parent = nullptr, *uf_size = nullptr, *deferred = nullptr, *minm = nullptr, *flag = nullptr,
+             *block_sums = nullptr;
+    // small device block: counters and statistics
+    uint32_t *dcount = nullptr;             // [0] ovf, [1..3] round counters, [4] n_edges
+    unsigned long long *dstat = nullptr;    // [0] max_abs [1] max_rel [2] pairs [3] max_cand [4] n_merges [5] K [6] maxbits..
+    int *derr = nullptr;                    // [0] sweep time-out, [1] collect retry, [2] non-finite
+    // events
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    nnm_stats stats{};
+    int64_t launch_base = 0;
+    nnm_status status = NNM_OK;
+    std::string err;
+};
+
+namespace {
+
+nnm_status fail(nnm_ctx *c, nnm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->status = s;
+        c->err = buf;
+    }
+    return s;
+}
+
+#define NNM_CUDA(c, call)                                                                            \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess)                                                                       \
+            return fail((c), e_ == cudaErrorMemoryAllocation ? NNM_ENOMEM : NNM_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                          \
+    } while (0)
+
+#define NNM_TRY(x)                         \
+    do {                                           \
+        nnm_status s_ = (x);                       \
+        if (s_ != NNM_OK) return s_;               \
+    } while (0)
+
+template <typename T>
+nnm_status dalloc(nnm_ctx *c, T **p, size_t count)
+{
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(c, NNM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    }
+    return NNM_OK;
+}
+
+template <typename T>
+void dfree(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Phase timer: a pair of CUDA events on the context's stream around a scope; the
+// elapsed time is added to a stats field.  Phases may nest.
+struct Phase {
+    nnm_ctx *c;
+    double *acc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Phase(nnm_ctx *c_, double *acc_) : c(c_), acc(acc_)
+    {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, c->stream);
+    }
+    ~Phase()
+    {
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *acc += ms;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+bool is_tensor(const nnm_ctx *c) { return c->prec != NNM_PREC_FP32; }
+
+// Column ranges per row tile: enough CTAs to fill the 152 SMs a few times.
+int choose_splits(const nnm_ctx *c, int64_t nslots)
+{
+    if (c->opt.col_split > 0) return c->opt.col_split < kMaxSplits ? c->opt.col_split : kMaxSplits;
+    const int64_t row_ctas = (nslots + kRowTile - 1) / kRowTile;
+    const int64_t target = is_tensor(c) ? 152 * 4 : 152 * 2 * 4;
+    int64_t s = (target + row_ctas - 1) / row_ctas;
+    const int64_t max_by_cols = (c->N + 2047) / 2048;   // at least 16 tiles per range
+    if (s > max_by_cols) s = max_by_cols;
+    if (s > kMaxSplits) s = kMaxSplits;
+    if (s < 1) s = 1;
+    return (int)s;
+}
+
+nnm_status ensure_cand(nnm_ctx *c, size_t entries)
+{
+    if (entries <= c->cand_cap) return NNM_OK;
+    NNM_TRY(dalloc(c, &c->cand_v, entries));
+    NNM_TRY(dalloc(c, &c->cand_j, entries));
+    c->cand_cap = entries;
+    return NNM_OK;
+}
+
+nnm_status ensure_ovf(nnm_ctx *c, size_t slots)
+{
+    if (slots <= c->ovf_cap) return NNM_OK;
+    NNM_TRY(dalloc(c, &c->ovf_row, slots));
+    NNM_TRY(dalloc(c, &c->ovf_thr, slots));
+    NNM_TRY(dalloc(c, &c->coll_cnt, slots));
+    c->ovf_cap = slots;
+    return NNM_OK;
+}
+
+nnm_status ensure_coll(nnm_ctx *c, size_t entries)
+{
+    if (entries <= c->coll_cap) return NNM_OK;
+    NNM_TRY(dalloc(c, &c->coll_j, entries));
+    NNM_TRY(dalloc(c, &c->coll_D, entries));
+    c->coll_cap = entries;
+    return NNM_OK;
+}
+
+SweepArgs base_sweep(nnm_ctx *c)
+{
+    SweepArgs a{};
+    a.Xs = c->Xs;
+    a.dp = c->dp;
+    a.XA = c->XA;
+    a.XB = c->XB;
+    a.kpad = c->kpad;
+    a.fp16 = c->fp16;
+    a.N = c->N;
+    a.col_begin = 0;
+    a.col_end = c->N;
+    a.err_flag = &c->derr[0];
+    return a;
+}
+
+nnm_status launch_sweep(nnm_ctx *c, const SweepArgs &a, bool collect)
+{
+    cudaError_t e = is_tensor(c) ? launch_sweep_tc(a, collect, c->stream)
+                                 : launch_sweep_fp32(a, c->d, collect, c->stream);
+    if (e != cudaSuccess) return fail(c, NNM_ECUDA, "candidate sweep launch: %s", cudaGetErrorString(e));
+    c->stats.sweep_launches += 1;
+    c->stats.pairs_evaluated += a.nslots * c->N;
+    return NNM_OK;
+}
+
+nnm_status check_sweep_error(nnm_ctx *c)
+{
+    int h = 0;
+    NNM_CUDA(c, cudaMemcpyAsync(&h, &c->derr[0], sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    NNM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (h) {
+        NNM_CUDA(c, cudaMemsetAsync(&c->derr[0], 0, sizeof(int), c->stream));
+        return fail(c, NNM_ETIMEOUT, "a bounded wait in the tensor-core sweep gave up");
+    }
+    return NNM_OK;
+}
+
+// Exact k nearest eligible columns of the given rows (rows == nullptr: all rows).
+// Eligible: j != i, and comp[j] != comp[i] if comp is given.  Results go to
+// res_j/res_D [row][k] (and res_n / res_exh if given).
+nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, const uint32_t *comp,
+                   uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh, bool full)
+{
+    if (nslots <= 0) return NNM_OK;
+    const int S = choose_splits(c, nslots);
+    const int64_t cps = round_up((c->N + S - 1) / S, 128);
+    const int splits = (int)((c->N + cps - 1) / cps);
+    NNM_TRY(ensure_cand(c, (size_t)nslots * splits * kListC));
+    NNM_TRY(ensure_ovf(c, (size_t)nslots));
+
+    SweepArgs sa = base_sweep(c);
+    sa.rows = rows;
+    sa.nslots = nslots;
+    sa.comp = comp;
+    sa.cols_per_split = cps;
+    sa.splits = splits;
+    sa.out_v = c->cand_v;
+    sa.out_j = c->cand_j;
+    {
+        Phase ph(c, &c->stats.ms_sweep);
+        if (full) NNM_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+        NNM_TRY(launch_sweep(c, sa, false));
+        if (full) NNM_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+    }
+    if (full) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->stats.sweep_ms_per_launch_full = ms;
+        c->stats.full_sweep_pairs = c->N * (c->N - 1);
+    }
+    if (is_tensor(c)) NNM_TRY(check_sweep_error(c));
+
+    uint32_t novf = 0;
+    {
+        Phase ph(c, &c->stats.ms_rerank);
+        NNM_CUDA(c, cudaMemsetAsync(&c->dcount[0], 0, sizeof(uint32_t), c->stream));
+        FinalizeArgs fa{};
+        fa.X = c->X;
+        fa.d = c->d;
+        fa.N = c->N;
+        fa.rows = rows;
+        fa.nslots = nslots;
+        fa.splits = splits;
+        fa.in_v = c->cand_v;
+        fa.in_j = c->cand_j;
+        fa.k = k;
+        fa.m = c->margin;
+        fa.res_j = res_j;
+        fa.res_D = res_D;
+        fa.res_n = res_n;
+        fa.res_exh = res_exh;
+        fa.ovf_cnt = &c->dcount[0];
+        fa.ovf_row = c->ovf_row;
+        fa.ovf_thr = c->ovf_thr;
+        fa.st_max_abs = &c->dstat[0];
+        fa.st_max_rel = &c->dstat[1];
+        fa.st_pairs = &c->dstat[2];
+        fa.st_max_cand = &c->dstat[3];
+        NNM_CUDA(c, launch_finalize(fa, c->stream));
+        NNM_CUDA(c, cudaMemcpyAsync(&novf, &c->dcount[0], sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (novf == 0) return NNM_OK;
+
+    // collect pass: every eligible column with value <= the row's threshold
+    c->stats.rows_overflowed += novf;
+    int64_t cap = is_tensor(c) ? 1024 : 256;
+    for (int attempt = 0;; ++attempt) {
+        if (cap > c->N) cap = c->N;
+        NNM_TRY(ensure_coll(c, (size_t)novf * cap));
+        SweepArgs ca = base_sweep(c);
+        ca.rows = c->ovf_row;
+        ca.nslots = novf;
+        ca.comp = comp;
+        const int S2 = choose_splits(c, novf);
+        ca.cols_per_split = round_up((c->N + S2 - 1) / S2, 128);
+        ca.splits = (int)((c->N + ca.cols_per_split - 1) / ca.cols_per_split);
+        ca.thr = c->ovf_thr;
+        ca.coll_cnt = c->coll_cnt;
+        ca.coll_j = c->coll_j;
+        ca.coll_cap = cap;
+        {
+            Phase ph(c, &c->stats.ms_sweep);
+            NNM_CUDA(c, cudaMemsetAsync(c->coll_cnt, 0, novf * sizeof(uint32_t), c->stream));
+            NNM_TRY(launch_sweep(c, ca, true));
+        }
+        if (is_tensor(c)) NNM_TRY(check_sweep_error(c));
+        int retry = 0;
+        {
+            Phase ph(c, &c->stats.ms_rerank);
+            NNM_CUDA(c, cudaMemsetAsync(&c->derr[1], 0, sizeof(int), c->stream));
+            CollectRerankArgs ra{};
+            ra.X = c->X;
+            ra.d = c->d;
+            ra.N = c->N;
+            ra.rows = c->ovf_row;
+            ra.n = novf;
+            ra.coll_cnt = c->coll_cnt;
+            ra.coll_j = c->coll_j;
+            ra.cap = cap;
+            ra.scratch_D = c->coll_D;
+            ra.k = k;
+            ra.res_j = res_j;
+            ra.res_D = res_D;
+            ra.res_n = res_n;
+            ra.res_exh = res_exh;
+            ra.retry_flag = &c->derr[1];
+            ra.st_pairs = &c->dstat[2];
+            ra.st_max_cand = &c->dstat[3];
+            NNM_CUDA(c, launch_collect_rerank(ra, c->stream));
+            NNM_CUDA(c, cudaMemcpyAsync(&retry, &c->derr[1], sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        }
+        if (!retry) break;
+        if (cap >= c->N || attempt > 8) return fail(c, NNM_ECUDA, "collect pass did not converge");
+        cap *= 4;
+    }
+    return NNM_OK;
+}
+
+void reset_stats(nnm_ctx *c)
+{
+    const double prep = c->stats.ms_prep;
+    const int32_t kp = c->stats.k_pad;
+    const double sc = c->stats.scale;
+    memset(&c->stats, 0, sizeof c->stats);
+    c->stats.ms_prep = prep;
+    c->stats.k_pad = kp;
+    c->stats.scale = sc;
+    c->stats.cache_k = c->kc;
+    c->launch_base = launches_so_far();
+    cudaMemsetAsync(c->dstat, 0, 4 * sizeof(unsigned long long), c->stream);
+}
+
+nnm_status read_stats(nnm_ctx *c)
+{
+    unsigned long long h[4];
+    NNM_CUDA(c, cudaMemcpyAsync(h, c->dstat, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    NNM_CUDA(c, cudaStreamSynchronize(c->stream));
+    double a, r;
+    memcpy(&a, &h[0], 8);
+    memcpy(&r, &h[1], 8);
+    c->stats.max_abs_err = a;
+    c->stats.max_rel_err = r;
+    c->stats.rerank_pairs = (int64_t)h[2];
+    c->stats.max_candidates = (int64_t)h[3];
+    c->stats.kernel_launches = launches_so_far() - c->launch_base;
+    return NNM_OK;
+}
+
+nnm_status prepare(nnm_ctx *c)
+{
+    cudaStream_t s = c->stream;
+    c->Npad = round_up(c->N, 256);
+    NNM_TRY(dalloc(c, &c->dcount, 8));
+    NNM_TRY(dalloc(c, &c->dstat, 16));
+    NNM_TRY(dalloc(c, &c->derr, 4));
+    NNM_CUDA(c, cudaMemsetAsync(c->dcount, 0, 8 * sizeof(uint32_t), s));
+    NNM_CUDA(c, cudaMemsetAsync(c->dstat, 0, 16 * sizeof(unsigned long long), s));
+    NNM_CUDA(c, cudaMemsetAsync(c->derr, 0, 4 * sizeof(int), s));
+
+    // "check correctness of the data array"
+    NNM_CUDA(c, launch_check_finite(c->X, c->N * c->d, &c->derr[2], s));
+    int bad = 0;
+    NNM_CUDA(c, cudaMemcpyAsync(&bad, &c->derr[2], sizeof(int), cudaMemcpyDeviceToHost, s));
+    NNM_CUDA(c, cudaStreamSynchronize(s));
+    if (bad) return fail(c, NNM_ENONFINITE, "X holds NaN or infinite values");
+
+    if (!is_tensor(c)) {
+        c->dp = (c->d + 3) & ~3;
+        NNM_TRY(dalloc(c, &c->Xs, (size_t)c->Npad * c->dp));
+        NNM_CUDA(c, launch_pad_fp32(c->X, c->N, c->d, c->dp, c->Npad, c->Xs, s));
+        const double u = 0x1p-24;
+        c->margin.tensor = 0;
+        c->margin.gamma = (c->d + 2) * u / (1.0 - (c->d + 2) * u);
+        c->margin.alpha = (c->d + 2) * 0x1p-149;
+        c->margin.inv_scale2 = 1.0;
+    } else {
+        c->fp16 = c->prec == NNM_PREC_FP16_RERANK;
+        c->kpad = (int)round_up(c->d + 6, 16);
+        const int mb = mean_blocks(c->N);
+        double *partial = nullptr, *mu = nullptr;
+        NNM_TRY(dalloc(c, &partial, (size_t)mb * c->d));
+        NNM_TRY(dalloc(c, &mu, (size_t)c->d));
+        NNM_CUDA(c, launch_mean(c->X, c->N, c->d, partial, mb, mu, s));
+        NNM_CUDA(c, launch_max_sqnorm(c->X, c->N, c->d, mu, &c->dstat[8], s));
+        unsigned long long mbits = 0;
+        NNM_CUDA(c, cudaMemcpyAsync(&mbits, &c->dstat[8], 8, cudaMemcpyDeviceToHost, s));
+        NNM_CUDA(c, cudaStreamSynchronize(s));
+        double M;
+        memcpy(&M, &mbits, 8);
+        // one power-of-two scale so that every |x_hat|^2 stays below 2^14 (FP16 range
+        // for the norm pieces and the accumulator well inside FP32)
+        c->scale = 1.0;
+        if (M > 0.0) c->scale = ldexp(1.0, (int)floor(log2(sqrt(16384.0 / M))));
+        NNM_TRY(dalloc(c, &c->XA, (size_t)c->Npad * c->kpad));
+        NNM_TRY(dalloc(c, &c->XB, (size_t)c->Npad * c->kpad));
+        NNM_TRY(dalloc(c, &c->r, (size_t)c->Npad));
+        NNM_TRY(dalloc(c, &c->P, (size_t)c->Npad));
+        NNM_TRY(dalloc(c, &c->E, (size_t)c->Npad));
+        NNM_CUDA(c, launch_tc_operands(c->X, c->N, c->d, mu, c->scale, c->fp16, c->kpad, c->Npad, c->XA, c->XB,
+                                       c->r, c->P, c->E, &c->dstat[9], s));
+        unsigned long long mx[3];
+        NNM_CUDA(c, cudaMemcpyAsync(mx, &c->dstat[9], sizeof mx, cudaMemcpyDeviceToHost, s));
+        NNM_CUDA(c, cudaStreamSynchronize(s));
+        cudaFree(partial);
+        cudaFree(mu);
+        c->margin.tensor = 1;
+        // FP32 accumulation of kpad exact products, order and rounding mode unknown:
+        // at most kpad additions, each off by < 2^-23 of the partial-sum magnitude
+        c->margin.gamma = (c->kpad + 2) * 0x1p-23;
+        c->margin.alpha = 0.0;
+        memcpy(&c->margin.R, &mx[0], 8);
+        memcpy(&c->margin.Pmax, &mx[1], 8);
+        memcpy(&c->margin.Emax, &mx[2], 8);
+        c->margin.inv_scale2 = 1.0 / (c->scale * c->scale);
+        c->margin.r = c->r;
+        c->margin.P = c->P;
+        c->margin.E = c->E;
+        c->stats.k_pad = c->kpad;
+        c->stats.scale = c->scale;
+    }
+    return NNM_OK;
+}
+
+nnm_status ensure_rounds(nnm_ctx *c)
+{
+    if (c->comp) return NNM_OK;
+    const int64_t N = c->N;
+    NNM_TRY(dalloc(c, &c->cache_j, (size_t)N * c->kc));
+    NNM_TRY(dalloc(c, &c->cache_D, (size_t)N * c->kc));
+    NNM_TRY(dalloc(c, &c->cache_n, (size_t)N));
+    NNM_TRY(dalloc(c, &c->cache_exh, (size_t)N));
+    NNM_TRY(dalloc(c, &c->parent, (size_t)N));
+    NNM_TRY(dalloc(c, &c->list, (size_t)N));
+    NNM_TRY(dalloc(c, &c->row_D, (size_t)N));
+    NNM_TRY(dalloc(c, &c->row_ab, (size_t)N));
+    NNM_TRY(dalloc(c, &c->best_D, (size_t)N));
+    NNM_TRY(dalloc(c, &c->best_ab, (size_t)N));
+    NNM_TRY(dalloc(c, &c->row_state, (size_t)N));
+    NNM_TRY(dalloc(c, &c->frozen, (size_t)N));
+    NNM_TRY(dalloc(c, &c->edges, (size_t)N));
+    NNM_TRY(dalloc(c, &c->edges_tmp, (size_t)N));
+    NNM_TRY(dalloc(c, &c->uf_parent, (size_t)N));
+    NNM_TRY(dalloc(c, &c->uf_size, (size_t)N));
+    NNM_TRY(dalloc(c, &c->deferred, (size_t)N));
+    NNM_TRY(dalloc(c, &c->minm, (size_t)N));
+    NNM_TRY(dalloc(c, &c->flag, (size_t)N));
+    NNM_TRY(dalloc(c, &c->block_sums, (size_t)labels_scratch_blocks(N)));
+    NNM_TRY(dalloc(c, &c->comp, (size_t)N));   // last: marks the set as allocated
+    return NNM_OK;
+}
+
+template <typename T>
+nnm_status read_dev(nnm_ctx *c, T *host, const T *dev)
+{
+    NNM_CUDA(c, cudaMemcpyAsync(host, dev, sizeof(T), cudaMemcpyDeviceToHost, c->stream));
+    NNM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NNM_OK;
+}
+
+// The merge tree: exact k-NN cache, then rounds until one component remains (or, with
+// freeze_at_cap, until no component has an admissible outgoing pair).
+nnm_status build_tree(nnm_ctx *c, double cap2)
+{
+    NNM_TRY(ensure_rounds(c));
+    cudaStream_t s = c->stream;
+    NNM_TRY(run_knn(c, nullptr, c->N, c->kc, nullptr, c->cache_j, c->cache_D, c->cache_n, c->cache_exh, true));
+
+    RoundState st{};
+    st.N = c->N;
+    st.k = c->kc;
+    st.comp = c->comp;
+    st.parent = c->parent;
+    st.cache_j = c->cache_j;
+    st.cache_D = c->cache_D;
+    st.cache_n = c->cache_n;
+    st.cache_exh = c->cache_exh;
+    st.row_D = c->row_D;
+    st.row_ab = c->row_ab;
+    st.row_state = c->row_state;
+    st.best_D = c->best_D;
+    st.best_ab = c->best_ab;
+    st.list = c->list;
+    st.counters = &c->dcount[1];
+    st.edges = c->edges;
+    st.n_edges = &c->dcount[4];
+    st.frozen = c->frozen;
+    st.cap2 = cap2;
+    {
+        Phase ph(c, &c->stats.ms_rounds);
+        NNM_CUDA(c, launch_round_init(st, s));
+        NNM_CUDA(c, cudaMemsetAsync(&c->dcount[1], 0, 4 * sizeof(uint32_t), s));
+    }
+    int64_t ncomp = c->N;
+    for (int round = 0; ncomp > 1; ++round) {
+        if (round > 64) return fail(c, NNM_ECUDA, "merge rounds did not converge");
+        c->stats.rounds = round + 1;
+        uint32_t nres = 0;
+        {
+            Phase ph(c, &c->stats.ms_rounds);
+            NNM_CUDA(c, launch_resolve(st, nullptr, c->N, s));
+            NNM_CUDA(c, launch_component_min(st, s));
+            NNM_CUDA(c, cudaMemsetAsync(&c->dcount[1], 0, sizeof(uint32_t), s));
+            NNM_CUDA(c, launch_flag_rescans(st, s));
+        }
+        NNM_TRY(read_dev(c, &nres, &c->dcount[1]));
+        if (nres > 0) {
+            c->stats.rows_rescanned += nres;
+            NNM_TRY(run_knn(c, c->list, nres, c->kc, c->comp, c->cache_j, c->cache_D, c->cache_n, c->cache_exh,
+                            false));
+            Phase ph(c, &c->stats.ms_rounds);
+            NNM_CUDA(c, launch_resolve(st, c->list, nres, s));
+            NNM_CUDA(c, launch_component_min(st, s));
+        }
+        uint32_t nedge = 0;
+        {
+            Phase ph(c, &c->stats.ms_rounds);
+            NNM_CUDA(c, cudaMemsetAsync(&c->dcount[2], 0, sizeof(uint32_t), s));
+            NNM_CUDA(c, launch_hook(st, s));
+        }
+        NNM_TRY(read_dev(c, &nedge, &c->dcount[2]));
+        if (nedge == 0) break;
+        {
+            Phase ph(c, &c->stats.ms_rounds);
+            for (int it = 0;; ++it) {
+                if (it > 64) return fail(c, NNM_ECUDA, "pointer jumping did not converge");
+                uint32_t changed = 0;
+                NNM_CUDA(c, cudaMemsetAsync(&c->dcount[3], 0, sizeof(uint32_t), s));
+                NNM_CUDA(c, launch_jump(st, s));
+                NNM_TRY(read_dev(c, &changed, &c->dcount[3]));
+                if (!changed) break;
+            }
+            NNM_CUDA(c, launch_relabel(st, s));
+        }
+        ncomp -= nedge;
+    }
+    uint32_t ne = 0;
+    NNM_TRY(read_dev(c, &ne, &c->dcount[4]));
+    c->n_tree = ne;
+    {
+        Phase ph(c, &c->stats.ms_sort);
+        NNM_CUDA(c, launch_sort_edges(c->edges, c->edges_tmp, c->n_tree, s, &c->tree));
+    }
+    return NNM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nnm_status_string(nnm_status s)
+{
+    switch (s) {
+    case NNM_OK: return "NNM_OK";
+    case NNM_EINVAL: return "NNM_EINVAL";
+    case NNM_ENONFINITE: return "NNM_ENONFINITE";
+    case NNM_ENOMEM: return "NNM_ENOMEM";
+    case NNM_ECUDA: return "NNM_ECUDA";
+    case NNM_ETIMEOUT: return "NNM_ETIMEOUT";
+    case NNM_EUNSUPPORTED: return "NNM_EUNSUPPORTED";
+    }
+    return "unknown";
+}
+
+nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metric, nnm_precision precision,
+                      void *cuda_stream, const nnm_options *options, nnm_ctx **out)
+{
+    if (!out) return NNM_EINVAL;
+    *out = nullptr;
+    if (!X_dev || N < 1 || N >= (int64_t(1) << 31) || d < 1 || d > 32) return NNM_EINVAL;
+    if (metric != NNM_EUCLIDEAN) return NNM_EUNSUPPORTED;
+    if (precision != NNM_PREC_FP32 && precision != NNM_PREC_BF16_RERANK && precision != NNM_PREC_FP16_RERANK)
+        return NNM_EUNSUPPORTED;
+    if (options && (options->cache_k < 0 || options->cache_k > 16 || options->col_split < 0)) return NNM_EINVAL;
+    nnm_ctx *c = new nnm_ctx();
+    c->X = X_dev;
+    c->N = N;
+    c->d = d;
+    c->prec = precision;
+    if (options) c->opt = *options;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->kc = c->opt.cache_k > 0 ? c->opt.cache_k : (precision == NNM_PREC_BF16_RERANK ? 2 : 8);
+    if (c->kc > N - 1) c->kc = N > 1 ? (int)(N - 1) : 1;
+    cudaGetDevice(&c->device);
+    cudaEventCreate(&c->ev0);
+    cudaEventCreate(&c->ev1);
+    nnm_status st;
+    {
+        Phase ph(c, &c->stats.ms_prep);
+        st = prepare(c);
+    }
+    if (st != NNM_OK) {
+        nnm_destroy(c);
+        return st;
+    }
+    *out = c;
+    return NNM_OK;
+}
+
+nnm_status nnm_nearest(nnm_ctx *c, int32_t k, uint32_t *idx_dev, double *D_dev)
+{
+    if (!c) return NNM_EINVAL;
+    c->err.clear();
+    c->status = NNM_OK;
+    if (!idx_dev || !D_dev) return fail(c, NNM_EINVAL, "null output buffer");
+    if (k < 1 || k > kMaxK || (int64_t)k >= c->N) return fail(c, NNM_EINVAL, "k=%d outside 1..min(24, N-1)", k);
+    reset_stats(c);
+    {
+        Phase total(c, &c->stats.ms_total);
+        NNM_TRY(run_knn(c, nullptr, c->N, k, nullptr, idx_dev, D_dev, nullptr, nullptr, true));
+    }
+    return read_stats(c);
+}
+
+nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *merges_dev, int64_t *n_merges_host,
+                       int32_t *labels_dev, int64_t *n_clusters_host)
+{
+    if (!c) return NNM_EINVAL;
+    c->err.clear();
+    c->status = NNM_OK;
+    if (!merges_dev || !n_merges_host || !labels_dev || !n_clusters_host)
+        return fail(c, NNM_EINVAL, "null output pointer");
+    if (c->N < 2) return fail(c, NNM_EINVAL, "nnm_cluster needs N >= 2");
+    nnm_restrictions r{};
+    if (restr) r = *restr;
+    if (r.semantics == 1) return fail(c, NNM_EUNSUPPORTED, "paper-literal semantics (1) is not provided");
+    if (r.semantics != 0) return fail(c, NNM_EINVAL, "semantics must be 0");
+    if (isnan(r.max_join_dist) || r.kl1_stop_clusters < 0 || r.kl2_max_pre_size < 0 || r.kl3_max_size < 0 ||
+        r.kl4_min_size < 0)
+        return fail(c, NNM_EINVAL, "negative restriction");
+    if (r.kl2_max_pre_size > 0 && r.kl3_max_size > 0 && r.kl3_max_size <= r.kl2_max_pre_size)
+        return fail(c, NNM_EINVAL, "KL3 must exceed KL2");
+    const double cap2 = (r.max_join_dist > 0.0 && isfinite(r.max_join_dist)) ? r.max_join_dist * r.max_join_dist
+                                                                             : INFINITY;
+    reset_stats(c);
+    {
+        Phase total(c, &c->stats.ms_total);
+        NNM_TRY(build_tree(c, c->opt.freeze_at_cap ? cap2 : INFINITY));
+        {
+            Phase ph(c, &c->stats.ms_restrict);
+            RestrictArgs ra{};
+            ra.edges = c->tree;
+            ra.m = c->n_tree;
+            ra.N = c->N;
+            ra.cap2 = cap2;
+            ra.kl1 = r.kl1_stop_clusters;
+            ra.kl2 = r.kl2_max_pre_size;
+            ra.kl3 = r.kl3_max_size;
+            ra.kl4 = r.kl4_min_size;
+            ra.uf_parent = c->uf_parent;
+            ra.uf_size = c->uf_size;
+            ra.deferred = c->deferred;
+            ra.merges = merges_dev;
+            ra.n_merges = &c->dstat[4];
+            ra.err_flag = &c->derr[3];
+            NNM_CUDA(c, launch_restrict(ra, c->stream));
+        }
+        {
+            Phase ph(c, &c->stats.ms_labels);
+            LabelArgs la{};
+            la.N = c->N;
+            la.uf_parent = c->uf_parent;
+            la.minm = c->minm;
+            la.flag = c->flag;
+            la.block_sums = c->block_sums;
+            la.labels = labels_dev;
+            la.K = &c->dstat[5];
+            NNM_CUDA(c, launch_labels(la, c->stream));
+        }
+    }
+    unsigned long long h[2];
+    NNM_CUDA(c, cudaMemcpyAsync(h, &c->dstat[4], sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    NNM_CUDA(c, cudaStreamSynchronize(c->stream));
+    *n_merges_host = (int64_t)h[0];
+    *n_clusters_host = (int64_t)h[1];
+    return read_stats(c);
+}
+
+nnm_status nnm_get_tree(nnm_ctx *c, nnm_edge *edges_dev, int64_t *n_edges_host)
+{
+    if (!c) return NNM_EINVAL;
+    if (!edges_dev || !n_edges_host) return fail(c, NNM_EINVAL, "null output pointer");
+    if (!c->tree) return fail(c, NNM_EINVAL, "no tree: call nnm_cluster first");
+    NNM_CUDA(c, cudaMemcpyAsync(edges_dev, c->tree, c->n_tree * sizeof(nnm_edge), cudaMemcpyDeviceToDevice,
+                                c->stream));
+    NNM_CUDA(c, cudaStreamSynchronize(c->stream));
+    *n_edges_host = c->n_tree;
+    return NNM_OK;
+}
+
+nnm_status nnm_get_stats(const nnm_ctx *c, nnm_stats *out)
+{
+    if (!c || !out) return NNM_EINVAL;
+    *out = c->stats;
+    return NNM_OK;
+}
+
+const char *nnm_last_error(const nnm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void nnm_destroy(nnm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    dfree(c->Xs);
+    dfree(c->XA);
+    dfree(c->XB);
+    dfree(c->r);
+    dfree(c->P);
+    dfree(c->E);
+    dfree(c->cand_v);
+    dfree(c->cand_j);
+    dfree(c->ovf_row);
+    dfree(c->ovf_thr);
+    dfree(c->coll_cnt);
+    dfree(c->coll_j);
+    dfree(c->coll_D);
+    dfree(c->cache_j);
+    dfree(c->cache_D);
+    dfree(c->cache_n);
+    dfree(c->cache_exh);
+    dfree(c->comp);
+    dfree(c->parent);
+    dfree(c->list);
+    dfree(c->row_D);
+    dfree(c->row_ab);
+    dfree(c->best_D);
+    dfree(c->best_ab);
+    dfree(c->row_state);
+    dfree(c->frozen);
+    dfree(c->edges);
+    dfree(c->edges_tmp);
+    dfree(c->uf_parent);
+    dfree(c->uf_size);
+    dfree(c->deferred);
+    dfree(c->minm);
+    dfree(c->flag);
+    dfree(c->block_sums);
+    dfree(c->dcount);
+    dfree(c->dstat);
+    dfree(c->derr);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+}
+
+}  // extern "C"

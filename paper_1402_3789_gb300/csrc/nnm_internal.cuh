@@ -1,0 +1,217 @@
+// nnm_internal.cuh -- internal declarations of the sm_103a NNM clustering library.
+//
+// Layout of the device workspace, kernel argument blocks and launch wrappers shared
+// between the translation units.  Nothing here is part of the C ABI (include/nnm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nnm.h"
+
+namespace nnm {
+
+// Process-wide count of kernel launches made by this library (read per call).
+void count_launches(int n);
+int64_t launches_so_far();
+
+constexpr uint32_t kInvalid = 0xFFFFFFFFu;
+constexpr int kListC = 32;        // candidates a sweep keeps per (row, column range)
+constexpr int kMaxK = 24;         // largest k of nnm_nearest / cache width
+constexpr int kRowTile = 256;     // rows per sweep CTA (both candidate paths)
+constexpr int kMaxSplits = 32;    // column ranges per row tile
+constexpr uint64_t kMaxKey = 0xFFFFFFFFFFFFFFFFull;
+
+// ---------------------------------------------------------------------------------
+// Candidate sweep (K1 FP32 direct / K2 tensor core): for each row slot, either keep
+// the kListC smallest candidate values per column range (top-C mode) or append every
+// eligible column whose value is <= the slot's threshold (collect mode).
+// ---------------------------------------------------------------------------------
+struct SweepArgs {
+    // operands
+    const float *Xs;          // FP32 path: [Npad][dp] padded copy of X
+    int dp;
+    const uint16_t *XA;       // tensor path: row operand, core-matrix interleaved [Npad][kpad]
+    const uint16_t *XB;       // tensor path: column operand, same layout
+    int kpad;
+    int fp16;                 // tensor path: 1 FP16 operands, 0 BF16
+    int64_t N;
+    // rows
+    const uint32_t *rows;     // nullptr: slot q is row q
+    int64_t nslots;
+    // eligibility
+    const uint32_t *comp;     // nullptr: every column j != i is eligible; else comp[j] != comp[i]
+    // columns
+    int64_t col_begin, col_end, cols_per_split;
+    int splits;
+    // top-C output: [nslots][splits][kListC]
+    float *out_v;
+    uint32_t *out_j;
+    // collect mode
+    const float *thr;         // per slot, values <= thr are appended
+    uint32_t *coll_cnt;       // per slot counters
+    uint32_t *coll_j;         // [nslots][coll_cap]
+    int64_t coll_cap;
+    // bounded waits of the tensor kernel
+    int *err_flag;
+};
+
+// Launch the FP32 direct sweep (template on d).
+cudaError_t launch_sweep_fp32(const SweepArgs &a, int d, bool collect, cudaStream_t s);
+// Launch the tcgen05 sweep.
+cudaError_t launch_sweep_tc(const SweepArgs &a, bool collect, cudaStream_t s);
+size_t sweep_tc_smem_bytes(int kpad);
+
+// ---------------------------------------------------------------------------------
+// Exact re-rank (K3)
+// ---------------------------------------------------------------------------------
+struct Margin {
+    int tensor;         // 0: FP32 direct candidates; 1: tensor-core candidates
+    double gamma;       // relative error bound of one candidate value
+    double alpha;       // absolute slack (underflow)
+    double R;           // tensor: max rounding radius over rows (scaled units)
+    double Pmax;        // tensor: max |x_hat| over rows
+    double Emax;        // tensor: max norm-split error over rows
+    double inv_scale2;  // 1 / scale^2 (tensor candidates are in scaled units)
+    const float *r;     // tensor: per-row rounding radius
+    const float *P;     // tensor: per-row |x_hat|
+    const float *E;     // tensor: per-row norm-split error
+};
+
+struct FinalizeArgs {
+    const float *X;            // user's rows [N][d]
+    int d;
+    int64_t N;
+    const uint32_t *rows;      // slot -> row (nullptr: identity)
+    int64_t nslots;
+    int splits;
+    const float *in_v;         // [nslots][splits][kListC]
+    const uint32_t *in_j;
+    int k;                     // results per row
+    Margin m;
+    // results (indexed by row)
+    uint32_t *res_j;           // [N][k]
+    double *res_D;             // [N][k]
+    uint8_t *res_n;            // valid results per row (nullable)
+    uint8_t *res_exh;          // 1: the results hold every eligible column (nullable)
+    // incomplete rows -> collect pass
+    uint32_t *ovf_cnt;         // single counter
+    uint32_t *ovf_row;         // [nslots] row index of each incomplete slot
+    float *ovf_thr;            // [nslots] its threshold (rounded up)
+    // statistics
+    unsigned long long *st_max_abs;   // double bits
+    unsigned long long *st_max_rel;
+    unsigned long long *st_pairs;
+    unsigned long long *st_max_cand;
+};
+
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s);
+
+struct CollectRerankArgs {
+    const float *X;
+    int d;
+    int64_t N;
+    const uint32_t *rows;      // collect slot p -> row index
+    int64_t n;                 // collect slots
+    const uint32_t *coll_cnt;  // [n]
+    const uint32_t *coll_j;    // [n][cap]
+    int64_t cap;
+    double *scratch_D;         // [n][cap]
+    int k;
+    uint32_t *res_j;
+    double *res_D;
+    uint8_t *res_n;
+    uint8_t *res_exh;
+    int *retry_flag;           // set when a slot collected more than cap
+    unsigned long long *st_pairs;
+    unsigned long long *st_max_cand;
+};
+
+cudaError_t launch_collect_rerank(const CollectRerankArgs &a, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// Preparation
+// ---------------------------------------------------------------------------------
+cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream_t s);
+cudaError_t launch_pad_fp32(const float *X, int64_t N, int d, int dp, int64_t Npad, float *Xs,
+                            cudaStream_t s);
+// column means in binary64 (deterministic order); partial: [blocks][d]
+cudaError_t launch_mean(const float *X, int64_t N, int d, double *partial, int blocks, double *mu,
+                        cudaStream_t s);
+int mean_blocks(int64_t N);
+cudaError_t launch_max_sqnorm(const float *X, int64_t N, int d, const double *mu,
+                              unsigned long long *out_bits, cudaStream_t s);
+cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale,
+                               int fp16, int kpad, int64_t Npad, uint16_t *XA, uint16_t *XB,
+                               float *r, float *P, float *E, unsigned long long *max_bits /*[3]*/,
+                               cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// Merge rounds (K4/K5)
+// ---------------------------------------------------------------------------------
+struct RoundState {
+    int64_t N;
+    int k;                         // cache width
+    uint32_t *comp;                // [N] component id (= root row id)
+    uint32_t *parent;              // [N] hook target per component root
+    const uint32_t *cache_j;       // [N][k]
+    const double *cache_D;
+    const uint8_t *cache_n;
+    const uint8_t *cache_exh;
+    unsigned long long *row_D;     // [N] key of the row's best outgoing candidate (D bits)
+    unsigned long long *row_ab;    // [N] (min << 32) | max
+    uint8_t *row_state;            // 0 none, 1 resolved, 2 unresolved (row_D/row_ab: bound)
+    unsigned long long *best_D;    // [N] per component
+    unsigned long long *best_ab;
+    uint32_t *list;                // [N] rescan rows
+    uint32_t *counters;            // [0] rescans, [1] edges this round, [2] jump changes
+    nnm_edge *edges;               // [N-1]
+    uint32_t *n_edges;             // device count
+    uint8_t *frozen;               // [N] per component root
+    double cap2;                   // freeze threshold (inf: none)
+};
+
+cudaError_t launch_round_init(RoundState &st, cudaStream_t s);
+cudaError_t launch_resolve(RoundState &st, const uint32_t *rows, int64_t nrows, cudaStream_t s);
+cudaError_t launch_component_min(RoundState &st, cudaStream_t s);
+cudaError_t launch_flag_rescans(RoundState &st, cudaStream_t s);
+cudaError_t launch_hook(RoundState &st, cudaStream_t s);
+cudaError_t launch_jump(RoundState &st, cudaStream_t s);
+cudaError_t launch_relabel(RoundState &st, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// Sort (K6), restriction walk (K7), labels (K8)
+// ---------------------------------------------------------------------------------
+cudaError_t launch_sort_edges(nnm_edge *e, nnm_edge *tmp, int64_t m, cudaStream_t s,
+                              nnm_edge **sorted_out);
+
+struct RestrictArgs {
+    const nnm_edge *edges;     // key-sorted tree edges
+    int64_t m;
+    int64_t N;
+    double cap2;               // inf: none
+    int64_t kl1, kl2, kl3, kl4;
+    uint32_t *uf_parent;       // [N] scratch
+    uint32_t *uf_size;         // [N] scratch
+    uint32_t *deferred;        // [m] scratch (KL4 second walk)
+    nnm_merge *merges;         // [N-1] out
+    unsigned long long *n_merges; // device out
+    int *err_flag;
+};
+
+cudaError_t launch_restrict(const RestrictArgs &a, cudaStream_t s);
+
+struct LabelArgs {
+    int64_t N;
+    uint32_t *uf_parent;       // union-find after the restriction walk
+    uint32_t *minm;            // [N] scratch
+    uint32_t *flag;            // [N] scratch (first member flags -> ranks)
+    uint32_t *block_sums;      // scratch
+    int32_t *labels;           // out
+    unsigned long long *K;     // device out
+};
+
+cudaError_t launch_labels(const LabelArgs &a, cudaStream_t s);
+int64_t labels_scratch_blocks(int64_t N);
+
+}  // namespace nnm

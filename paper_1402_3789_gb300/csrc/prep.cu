@@ -1,0 +1,245 @@
+// prep.cu -- K0: checks and operand preparation for the candidate sweeps.
+//
+// The paper's main module checks the data array and fills auxiliary working fields
+// ("Objectives of the main module"); here that is: reject non-finite values, build the
+// padded FP32 copy for the direct-difference sweep, and, for the tensor-core sweeps,
+// the centred, scaled, rounded operands with the per-row bounds that make the later
+// exact re-rank provably complete.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "nnm_internal.cuh"
+
+namespace nnm {
+
+__global__ void k_check_finite(const float *__restrict__ X, int64_t n, int *flag)
+{
+    int bad = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(X[q]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream_t s)
+{
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_check_finite<<<blocks, 256, 0, s>>>(X, n, flag);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Padded FP32 copy: rows [N, Npad) get a large value in every feature so that their
+// candidate values are large; they are excluded by index anyway.
+__global__ void k_pad_fp32(const float *__restrict__ X, int64_t N, int d, int dp, int64_t Npad,
+                           float *__restrict__ Xs)
+{
+    int64_t total = Npad * dp;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = q / dp;
+        int k = (int)(q - i * dp);
+        float v = 0.0f;
+        if (i >= N) v = k < d ? 1.0e18f : 0.0f;
+        else if (k < d) v = X[i * d + k];
+        Xs[q] = v;
+    }
+}
+
+cudaError_t launch_pad_fp32(const float *X, int64_t N, int d, int dp, int64_t Npad, float *Xs,
+                            cudaStream_t s)
+{
+    int64_t total = Npad * dp;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_pad_fp32<<<blocks, 256, 0, s>>>(X, N, d, dp, Npad, Xs);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Column means: block b sums rows [b*chunk, (b+1)*chunk) in a fixed order, the final
+// kernel adds the block sums in block order: the result does not depend on timing.
+int mean_blocks(int64_t N)
+{
+    int64_t b = (N + 2047) / 2048;
+    if (b > 1024) b = 1024;
+    return (int)(b < 1 ? 1 : b);
+}
+
+__global__ void __launch_bounds__(256) k_mean_partial(const float *__restrict__ X, int64_t N, int d,
+                                                      double *__restrict__ partial)
+{
+    __shared__ double red[256];
+    int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
+    int64_t lo = (int64_t)blockIdx.x * chunk;
+    int64_t hi = lo + chunk < N ? lo + chunk : N;
+    for (int k = 0; k < d; ++k) {
+        double acc = 0.0;
+        for (int64_t i = lo + threadIdx.x; i < hi; i += 256) acc += (double)X[i * d + k];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int w = 128; w > 0; w >>= 1) {
+            if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * d + k] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_mean_final(const double *__restrict__ partial, int blocks, int d, int64_t N,
+                             double *__restrict__ mu)
+{
+    int k = threadIdx.x;
+    if (k >= d) return;
+    double acc = 0.0;
+    for (int b = 0; b < blocks; ++b) acc += partial[(int64_t)b * d + k];
+    mu[k] = acc / (double)N;
+}
+
+cudaError_t launch_mean(const float *X, int64_t N, int d, double *partial, int blocks, double *mu,
+                        cudaStream_t s)
+{
+    k_mean_partial<<<blocks, 256, 0, s>>>(X, N, d, partial);
+    count_launches(1);
+    k_mean_final<<<1, 32, 0, s>>>(partial, blocks, d, N, mu);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v)
+{
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void k_max_sqnorm(const float *__restrict__ X, int64_t N, int d, const double *__restrict__ mu,
+                             unsigned long long *out)
+{
+    double best = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double e = (double)X[i * d + k] - mu[k];
+            s2 += e * e;
+        }
+        best = fmax(best, s2);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, best);
+}
+
+cudaError_t launch_max_sqnorm(const float *X, int64_t N, int d, const double *mu,
+                              unsigned long long *out_bits, cudaStream_t s)
+{
+    int blocks = (int)((N + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_max_sqnorm<<<blocks, 256, 0, s>>>(X, N, d, mu, out_bits);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Round a binary64 value to the 16-bit operand format (round to nearest even) and
+// return it both as bits and as its exact binary64 value.
+__device__ __forceinline__ uint16_t round16(double v, int fp16, double *exact)
+{
+    if (fp16) {
+        __half h = __double2half(v);
+        *exact = (double)__half2float(h);
+        return __half_as_ushort(h);
+    }
+    __nv_bfloat16 h = __double2bfloat16(v);
+    *exact = (double)__bfloat162float(h);
+    return __bfloat16_as_ushort(h);
+}
+
+// Element offset of (row i, K index k) in the core-matrix interleaved operand layout:
+// 8-row groups, each holding kpad/8 core matrices of 8 rows x 8 elements (16 bytes).
+__device__ __forceinline__ int64_t il_offset(int64_t i, int k, int kpad)
+{
+    return (((i >> 3) * (kpad >> 3) + (k >> 3)) * 8 + (i & 7)) * 8 + (k & 7);
+}
+
+// Tensor-core operands.  With y = (x - mu) * scale (scale a power of two) and x_hat
+// its rounding, the accumulator of the row operand A_i = [x_hat_i, 1, 1, 1, a_i]
+// against the column operand B_j = [-2 x_hat_j, a_j, 1, 1, 1] is
+//     |x_hat_i|^2 + |x_hat_j|^2 - 2 x_hat_i . x_hat_j  =  |x_hat_i - x_hat_j|^2
+// where a = (a1, a2, a3) splits the binary64 norm |x_hat|^2 into three 16-bit values.
+// Per row: r = |x_hat - y| (rounding radius, rounded up), P = |x_hat|, E = the split's
+// residual.  These bound the candidate error in the re-rank's completeness test.
+__global__ void k_tc_operands(const float *__restrict__ X, int64_t N, int d, const double *__restrict__ mu,
+                              double scale, int fp16, int kpad, int64_t Npad, uint16_t *__restrict__ XA,
+                              uint16_t *__restrict__ XB, float *__restrict__ r_out, float *__restrict__ P_out,
+                              float *__restrict__ E_out, unsigned long long *max_bits)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Npad) return;
+    const uint16_t one = fp16 ? (uint16_t)0x3C00 : (uint16_t)0x3F80;
+    if (i >= N) {
+        // padding column: a huge accumulator; padding row: zeros (never read back)
+        const uint16_t big = fp16 ? (uint16_t)0x7800 /* 32768 */ : (uint16_t)0x7180 /* 2^100 */;
+        for (int k = 0; k < kpad; ++k) {
+            XA[il_offset(i, k, kpad)] = 0;
+            XB[il_offset(i, k, kpad)] = (k >= d && k < d + 3) ? big : (uint16_t)0;
+        }
+        return;
+    }
+    double rr = 0.0, n = 0.0, ynorm2 = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double y = ((double)X[i * d + k] - mu[k]) * scale;
+        double h;
+        uint16_t bits = round16(y, fp16, &h);
+        rr += (h - y) * (h - y);
+        n += h * h;
+        ynorm2 += y * y;
+        XA[il_offset(i, k, kpad)] = bits;
+        // -2 * h is exact in either format (sign flip, exponent + 1)
+        double h2;
+        XB[il_offset(i, k, kpad)] = round16(-2.0 * h, fp16, &h2);
+    }
+    double a1, a2, a3;
+    uint16_t b1 = round16(n, fp16, &a1);
+    double rem = n - a1;
+    uint16_t b2 = round16(rem, fp16, &a2);
+    double rem2 = rem - a2;
+    uint16_t b3 = round16(rem2, fp16, &a3);
+    double E = fabs(rem2 - a3);
+    for (int k = d; k < kpad; ++k) {
+        uint16_t va = 0, vb = 0;
+        if (k < d + 3) {
+            va = one;
+            vb = k == d ? b1 : (k == d + 1 ? b2 : b3);
+        } else if (k < d + 6) {
+            va = k == d + 3 ? b1 : (k == d + 4 ? b2 : b3);
+            vb = one;
+        }
+        XA[il_offset(i, k, kpad)] = va;
+        XB[il_offset(i, k, kpad)] = vb;
+    }
+    // rounding radius: |x_hat - y| plus the binary64 error of (x - mu) * scale, both
+    // enlarged by a relative 1e-12 for the roundings of these bound computations
+    double r = (sqrt(rr) + sqrt(ynorm2) * 0x1p-52) * (1.0 + 1e-12) + 1e-300;
+    double P = sqrt(n) * (1.0 + 1e-12);
+    E = E * (1.0 + 1e-12);
+    float rf = __double2float_ru(r), Pf = __double2float_ru(P), Ef = __double2float_ru(E);
+    r_out[i] = rf;
+    P_out[i] = Pf;
+    E_out[i] = Ef;
+    atomic_max_nonneg(&max_bits[0], (double)rf);
+    atomic_max_nonneg(&max_bits[1], (double)Pf);
+    atomic_max_nonneg(&max_bits[2], (double)Ef);
+}
+
+cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale, int fp16,
+                               int kpad, int64_t Npad, uint16_t *XA, uint16_t *XB, float *r, float *P,
+                               float *E, unsigned long long *max_bits, cudaStream_t s)
+{
+    int blocks = (int)((Npad + 255) / 256);
+    k_tc_operands<<<blocks, 256, 0, s>>>(X, N, d, mu, scale, fp16, kpad, Npad, XA, XB, r, P, E, max_bits);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace nnm

@@ -1,0 +1,245 @@
+// rerank.cu -- K3: exact binary64 re-rank of the sweep candidates.
+//
+// The paper selects the P pairs with the smallest distance and sorts them ("General
+// description of the algorithm for constructing the set of minimum distances").  Here
+// each row's candidates from the FP32 or tensor-core sweep are re-ranked with the exact
+// squared distance of Eq. (1),
+//     D(i,j) = ((t_0 + t_1) + ...) + t_{d-1},  t_k = e_k*e_k,  e_k = x_ik - x_jk,
+// every operation IEEE binary64 round-to-nearest without contraction, and the k
+// smallest (D, j) are kept.  Completeness: a candidate value v approximates the exact
+// squared distance within a proven bound; from the k-th smallest v the re-rank derives a
+// threshold T such that every column of the exact top k has v <= T.  If a column range
+// kept kListC values all <= T, values above may have been dropped, and the row goes to
+// the collect pass instead (every eligible column with v <= T).
+#include "nnm_internal.cuh"
+
+namespace nnm {
+
+namespace {
+
+constexpr int kFinWarps = 4;
+
+__device__ __forceinline__ double canon_D(const float *__restrict__ xi, const float *__restrict__ xj, int d)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const double e = __dsub_rn((double)xi[k], (double)xj[k]);
+        s = __dadd_rn(s, __dmul_rn(e, e));
+    }
+    return s;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v)
+{
+    if (p) atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// Threshold T from the k-th smallest candidate value vk (see the file comment).
+__device__ double threshold(const Margin &m, uint32_t i, float vk)
+{
+    if (!(vk < INFINITY)) return INFINITY;
+    const double grow = 1.0 + 1e-12;
+    if (!m.tensor) {
+        // FP32 direct: |v - s| <= gamma*s + alpha, s the exact squared distance
+        const double us = ((double)vk + m.alpha) / (1.0 - m.gamma) * grow;
+        return (us * (1.0 + m.gamma) + m.alpha) * grow;
+    }
+    // tensor core (scaled units): |v - |x_hat_i - x_hat_j|^2| <= eps_i and
+    // | |x_hat_i - x_hat_j| - scale*sqrt(s) | <= r_i + r_j
+    const double Pi = (double)m.P[i];
+    const double eps = m.gamma * (Pi + m.Pmax) * (Pi + m.Pmax) + (double)m.E[i] + m.Emax;
+    const double rr = (double)m.r[i] + m.R;
+    const double U = (sqrt((double)vk + eps) + rr) * grow;
+    return ((U + rr) * (U + rr) + eps) * grow;
+}
+
+struct Best {
+    double D;
+    uint32_t j;
+    int e;
+};
+
+__device__ __forceinline__ bool less_dj(double D1, uint32_t j1, double D2, uint32_t j2)
+{
+    return D1 < D2 || (D1 == D2 && j1 < j2);
+}
+
+__device__ __forceinline__ Best warp_min(Best b)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Best c;
+        c.D = __shfl_xor_sync(0xffffffffu, b.D, o);
+        c.j = __shfl_xor_sync(0xffffffffu, b.j, o);
+        c.e = __shfl_xor_sync(0xffffffffu, b.e, o);
+        if (less_dj(c.D, c.j, b.D, b.j)) b = c;
+    }
+    return b;
+}
+
+// Pick the k smallest (D, j) of n entries held in (wD, wj) -- consumed entries get
+// D = +inf -- and write them to the row's result slots.
+__device__ void select_topk(double *wD, uint32_t *wj, int n, int k, uint32_t i, uint32_t *res_j,
+                           double *res_D, int *n_out)
+{
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    for (int m = 0; m < k; ++m) {
+        Best b = {INFINITY, kInvalid, -1};
+        for (int e = lane; e < n; e += 32)
+            if (wD[e] < INFINITY && less_dj(wD[e], wj[e], b.D, b.j)) b = {wD[e], wj[e], e};
+        b = warp_min(b);
+        if (lane == 0) {
+            res_j[(int64_t)i * k + m] = b.j;
+            res_D[(int64_t)i * k + m] = b.D;
+        }
+        if (b.e < 0) continue;
+        ++cnt;
+        if (lane == 0) wD[b.e] = INFINITY;
+        __syncwarp();
+    }
+    *n_out = cnt;
+}
+
+__global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs a)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_ent = a.splits * kListC;
+    double *wD = reinterpret_cast<double *>(smem) + (size_t)warp * n_ent;
+    float *wv = reinterpret_cast<float *>(reinterpret_cast<double *>(smem) + (size_t)kFinWarps * n_ent) +
+                (size_t)warp * n_ent;
+    uint32_t *wj = reinterpret_cast<uint32_t *>(reinterpret_cast<float *>(reinterpret_cast<double *>(smem) +
+                                                                          (size_t)kFinWarps * n_ent) +
+                                                (size_t)kFinWarps * n_ent) +
+                   (size_t)warp * n_ent;
+    const int64_t q = (int64_t)blockIdx.x * kFinWarps + warp;
+    if (q >= a.nslots) return;
+    const uint32_t i = a.rows ? a.rows[q] : (uint32_t)q;
+    const float *vin = a.in_v + q * n_ent;
+    const uint32_t *jin = a.in_j + q * n_ent;
+    for (int e = lane; e < n_ent; e += 32) {
+        wv[e] = vin[e];
+        wj[e] = jin[e];
+    }
+    __syncwarp();
+    // valid entries per column range (lists are sorted, invalid ones at the end)
+    int cnt = 0;
+    if (lane < a.splits)
+        for (int m = 0; m < kListC; ++m) cnt += wj[lane * kListC + m] != kInvalid;
+    // k-th smallest value over all ranges: k-way merge of the sorted lists
+    int head = 0, taken = 0;
+    float vk = INFINITY;
+    for (int m = 0; m < a.k; ++m) {
+        float hv = (lane < a.splits && head < cnt) ? wv[lane * kListC + head] : INFINITY;
+        int hl = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float ov = __shfl_xor_sync(0xffffffffu, hv, o);
+            int ol = __shfl_xor_sync(0xffffffffu, hl, o);
+            if (ov < hv || (ov == hv && ol < hl)) {
+                hv = ov;
+                hl = ol;
+            }
+        }
+        if (!(hv < INFINITY)) break;
+        vk = hv;
+        ++taken;
+        if (lane == hl) ++head;
+    }
+    const double T = threshold(a.m, i, taken < a.k ? INFINITY : vk);
+    const bool ok = lane >= a.splits || cnt < kListC || (double)wv[lane * kListC + kListC - 1] > T;
+    const int total = __reduce_add_sync(0xffffffffu, lane < a.splits ? cnt : 0);
+    if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) {
+            uint32_t p = atomicAdd(a.ovf_cnt, 1u);
+            a.ovf_row[p] = i;
+            a.ovf_thr[p] = __double2float_ru(T);
+        }
+        return;
+    }
+    const float *xi = a.X + (int64_t)i * a.d;
+    int ncand = 0;
+    double emax_abs = 0.0, emax_rel = 0.0;
+    for (int e = lane; e < n_ent; e += 32) {
+        const uint32_t j = wj[e];
+        double D = INFINITY;
+        if (j != kInvalid && (double)wv[e] <= T) {
+            D = canon_D(xi, a.X + (int64_t)j * a.d, a.d);
+            ++ncand;
+            const double err = fabs((double)wv[e] * a.m.inv_scale2 - D);
+            emax_abs = fmax(emax_abs, err);
+            if (D > 0.0) emax_rel = fmax(emax_rel, err / D);
+        }
+        wD[e] = D;
+    }
+    __syncwarp();
+    int n_out;
+    select_topk(wD, wj, n_ent, a.k, i, a.res_j, a.res_D, &n_out);
+    const int nc = __reduce_add_sync(0xffffffffu, ncand);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        emax_abs = fmax(emax_abs, __shfl_xor_sync(0xffffffffu, emax_abs, o));
+        emax_rel = fmax(emax_rel, __shfl_xor_sync(0xffffffffu, emax_rel, o));
+    }
+    if (lane == 0) {
+        if (a.res_n) a.res_n[i] = (uint8_t)n_out;
+        if (a.res_exh) a.res_exh[i] = (uint8_t)(total <= a.k);
+        atomic_max_nonneg(a.st_max_abs, emax_abs);
+        atomic_max_nonneg(a.st_max_rel, emax_rel);
+        if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nc);
+        if (a.st_max_cand) atomicMax(a.st_max_cand, (unsigned long long)nc);
+    }
+}
+
+__global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const CollectRerankArgs a)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t p = (int64_t)blockIdx.x * kFinWarps + warp;
+    if (p >= a.n) return;
+    const uint32_t i = a.rows[p];
+    const uint32_t cnt = a.coll_cnt[p];
+    if ((int64_t)cnt > a.cap) {
+        if (lane == 0) atomicExch(a.retry_flag, 1);
+        return;
+    }
+    const float *xi = a.X + (int64_t)i * a.d;
+    double *wD = a.scratch_D + p * a.cap;
+    uint32_t *wj = const_cast<uint32_t *>(a.coll_j) + p * a.cap;
+    for (uint32_t e = lane; e < cnt; e += 32) wD[e] = canon_D(xi, a.X + (int64_t)wj[e] * a.d, a.d);
+    __syncwarp();
+    __threadfence_block();
+    int n_out;
+    select_topk(wD, wj, (int)cnt, a.k, i, a.res_j, a.res_D, &n_out);
+    if (lane == 0) {
+        if (a.res_n) a.res_n[i] = (uint8_t)n_out;
+        if (a.res_exh) a.res_exh[i] = (uint8_t)((int)cnt < a.k);
+        if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)cnt);
+        if (a.st_max_cand) atomicMax(a.st_max_cand, (unsigned long long)cnt);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s)
+{
+    if (a.nslots <= 0) return cudaSuccess;
+    const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4);
+    cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)((a.nslots + kFinWarps - 1) / kFinWarps);
+    k_finalize<<<blocks, kFinWarps * 32, smem, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collect_rerank(const CollectRerankArgs &a, cudaStream_t s)
+{
+    if (a.n <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((a.n + kFinWarps - 1) / kFinWarps);
+    k_collect_rerank<<<blocks, kFinWarps * 32, 0, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace nnm

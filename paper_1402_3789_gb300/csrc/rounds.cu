@@ -1,0 +1,221 @@
+// rounds.cu -- K4/K5: merge rounds on the device.
+//
+// The paper joins clusters along minimal pairs, skipping pairs that already lie
+// inside one cluster ("General description of the algorithm for constructing the set
+// of minimum distances").  On the GPU the same tree (the unique minimum spanning tree
+// under key order) is grown in rounds: every component finds its smallest outgoing
+// pair (key order), every component hooks onto the component at the other end (of a
+// mutual pair, the smaller id stays root), and pointer jumping flattens the hooks.
+// Each selected pair is a tree edge by the cut property; each is emitted once.
+//
+// Each row's exact k nearest neighbours (cache) answer most rows' "nearest neighbour
+// outside my component" without a sweep: the first cached neighbour outside the
+// component is the answer, because all columns outside the cache are farther.  A row
+// whose whole cache lies inside its component only bounds its answer from below (by
+// its last cached key); it is rescanned only if that bound is below its component's
+// best resolved key.
+#include "nnm_internal.cuh"
+
+namespace nnm {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ unsigned long long pack_ab(uint32_t i, uint32_t j)
+{
+    const uint32_t a = i < j ? i : j, b = i < j ? j : i;
+    return ((unsigned long long)a << 32) | b;
+}
+
+__device__ __forceinline__ bool key_less(unsigned long long d1, unsigned long long ab1, unsigned long long d2,
+                                         unsigned long long ab2)
+{
+    return d1 < d2 || (d1 == d2 && ab1 < ab2);
+}
+
+inline unsigned grid_for(int64_t n)
+{
+    int64_t b = (n + kThreads - 1) / kThreads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+__global__ void k_round_init(RoundState st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.N) return;
+    st.comp[i] = (uint32_t)i;
+    st.parent[i] = (uint32_t)i;
+    st.frozen[i] = 0;
+}
+
+// Per row: the key of its nearest neighbour outside its component, from the cache.
+__global__ void k_resolve(RoundState st, const uint32_t *__restrict__ rows, int64_t nrows)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nrows) return;
+    const uint32_t i = rows ? rows[q] : (uint32_t)q;
+    const uint32_t c = st.comp[i];
+    if (st.frozen[c]) {
+        st.row_state[i] = 0;
+        return;
+    }
+    const int n = st.cache_n[i];
+    const uint32_t *cj = st.cache_j + (int64_t)i * st.k;
+    const double *cD = st.cache_D + (int64_t)i * st.k;
+    for (int m = 0; m < n; ++m) {
+        const uint32_t j = cj[m];
+        if (st.comp[j] != c) {
+            st.row_D[i] = (unsigned long long)__double_as_longlong(cD[m]);
+            st.row_ab[i] = pack_ab(i, j);
+            st.row_state[i] = 1;
+            return;
+        }
+    }
+    if (st.cache_exh[i] || n == 0) {
+        st.row_state[i] = 0;
+        return;
+    }
+    // lower bound: every column not cached has a larger key than the last cached one
+    st.row_D[i] = (unsigned long long)__double_as_longlong(cD[n - 1]);
+    st.row_ab[i] = pack_ab(i, cj[n - 1]);
+    st.row_state[i] = 2;
+}
+
+__global__ void k_best_reset(RoundState st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.N) return;
+    st.best_D[i] = kMaxKey;
+    st.best_ab[i] = kMaxKey;
+}
+
+__global__ void k_best_d(RoundState st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.N || st.row_state[i] != 1) return;
+    atomicMin(&st.best_D[st.comp[i]], st.row_D[i]);
+}
+
+__global__ void k_best_ab(RoundState st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.N || st.row_state[i] != 1) return;
+    const uint32_t c = st.comp[i];
+    if (st.row_D[i] == st.best_D[c]) atomicMin(&st.best_ab[c], st.row_ab[i]);
+}
+
+__global__ void k_flag(RoundState st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.N || st.row_state[i] != 2) return;
+    const uint32_t c = st.comp[i];
+    if (key_less(st.row_D[i], st.row_ab[i], st.best_D[c], st.best_ab[c])) {
+        const uint32_t p = atomicAdd(&st.counters[0], 1u);
+        st.list[p] = (uint32_t)i;
+    }
+}
+
+// Hook every component root onto the component at the far end of its best pair.
+__global__ void k_hook(RoundState st)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.N || st.comp[c] != (uint32_t)c) return;   // roots only
+    st.parent[c] = (uint32_t)c;
+    if (st.frozen[c] || st.best_D[c] == kMaxKey) return;
+    const double D = __longlong_as_double((long long)st.best_D[c]);
+    if (D > st.cap2) {
+        st.frozen[c] = 1;   // nothing within the cap leaves this component
+        return;
+    }
+    const uint32_t a = (uint32_t)(st.best_ab[c] >> 32), b = (uint32_t)(st.best_ab[c] & 0xFFFFFFFFu);
+    const uint32_t other = st.comp[a] == (uint32_t)c ? b : a;
+    const uint32_t c2 = st.comp[other];
+    const bool mutual = st.best_D[c2] == st.best_D[c] && st.best_ab[c2] == st.best_ab[c];
+    if (mutual && (uint32_t)c < c2) return;   // the smaller id of a mutual pair stays root
+    st.parent[c] = c2;
+    const uint32_t e = atomicAdd(st.n_edges, 1u);
+    nnm_edge ed;
+    ed.a = a;
+    ed.b = b;
+    ed.D = D;
+    st.edges[e] = ed;
+    atomicAdd(&st.counters[1], 1u);
+}
+
+__global__ void k_jump(RoundState st)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= st.N || st.comp[c] != (uint32_t)c) return;
+    const uint32_t p = st.parent[c];
+    const uint32_t pp = st.parent[p];
+    if (pp != p) {
+        st.parent[c] = pp;
+        st.counters[2] = 1u;
+    }
+}
+
+__global__ void k_relabel(RoundState st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.N) return;
+    st.comp[i] = st.parent[st.comp[i]];
+}
+
+}  // namespace
+
+cudaError_t launch_round_init(RoundState &st, cudaStream_t s)
+{
+    k_round_init<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resolve(RoundState &st, const uint32_t *rows, int64_t nrows, cudaStream_t s)
+{
+    if (nrows <= 0) return cudaSuccess;
+    k_resolve<<<grid_for(nrows), kThreads, 0, s>>>(st, rows, nrows);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_component_min(RoundState &st, cudaStream_t s)
+{
+    k_best_reset<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    k_best_d<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    k_best_ab<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_rescans(RoundState &st, cudaStream_t s)
+{
+    k_flag<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hook(RoundState &st, cudaStream_t s)
+{
+    k_hook<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jump(RoundState &st, cudaStream_t s)
+{
+    k_jump<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relabel(RoundState &st, cudaStream_t s)
+{
+    k_relabel<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace nnm

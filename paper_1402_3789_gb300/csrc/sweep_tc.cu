@@ -1,0 +1,438 @@
+// sweep_tc.cu -- K2: all-pairs candidate sweep on the 5th-generation tensor cores.
+//
+// Candidate values c~(i,j) = |x_hat_i - x_hat_j|^2 come out of one tcgen05 MMA chain
+// per tile: the row operand A_i = [x_hat_i, 1,1,1, a_i] and column operand
+// B_j = [-2 x_hat_j, a_j, 1,1,1] (prepared by k_tc_operands, K padded to kpad) give
+// |x_hat_i|^2 + |x_hat_j|^2 - 2 x_hat_i.x_hat_j directly in the FP32 accumulator, so
+// the epilogue is a compare against the row's threshold (a 3-input min over 32
+// values, then the rare slow path) -- the fused "distance + minimum selection" of the
+// paper's second and third parallel items.
+//
+// CTA = 256 rows (two M=128 MMAs sharing each B tile) x one column range, 320 threads:
+//   warps 0-7  epilogue, one row per thread (TMEM lane quadrant = warp % 4, half = warp / 4)
+//   warp 8     MMA issuer (one elected thread); also allocates / frees TMEM
+//   warp 9     producer: 1-D bulk copies (cp.async.bulk) of 128-column B tiles into an
+//              S-stage shared-memory ring; the operand is stored in HBM already in the
+//              core-matrix layout the MMA reads, so each tile is one contiguous copy.
+// TMEM: 512 columns = 2 accumulator buffers x 2 row halves x 128 columns (fp32).
+// Every wait is bounded (global timer); on time-out the CTA raises the error flag,
+// drains its own copies and MMAs with bounded waits, frees TMEM and exits.
+#include "nnm_internal.cuh"
+
+namespace nnm {
+
+namespace {
+
+constexpr int kEpiWarps = 8;
+constexpr int kThreadsTc = (kEpiWarps + 2) * 32;
+constexpr int kMmaWarp = 8;
+constexpr int kProdWarp = 9;
+constexpr int kBN = 128;          // columns per B tile
+constexpr int kStages = 8;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on a phase parity.  Returns false if the wait gave up (time-out, or
+// another role of this CTA already aborted).
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 0) {
+            if (*abort_flag) return false;
+            if (global_ns() - t0 > kWaitNs) return false;
+        }
+        if (it > 64) __nanosleep(128);
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle (canonical core-matrix layout):
+// start >> 4 | LBO (K-direction core-matrix stride) >> 4 << 16 | SBO (8-row-group
+// stride) >> 4 << 32 | version 1 << 46 | layout SWIZZLE_NONE (0) << 61.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = F16 (0) or BF16 (1), both K-major,
+// N = 128, M = 128.
+__device__ __forceinline__ uint32_t instr_desc(int fp16)
+{
+    const uint32_t fmt = fp16 ? 0u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+template <int C>
+__device__ __forceinline__ void list_insert(float (&lv)[C], uint32_t (&lj)[C], float v, uint32_t j)
+{
+#pragma unroll
+    for (int m = 0; m < C; ++m) {
+        bool sw = v < lv[m];
+        float tv = sw ? lv[m] : v;
+        uint32_t tj = sw ? lj[m] : j;
+        lv[m] = sw ? v : lv[m];
+        lj[m] = sw ? j : lj[m];
+        v = tv;
+        j = tj;
+    }
+}
+
+struct __align__(8) TcShared {
+    uint64_t full[kStages];
+    uint64_t empty[kStages];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+template <bool COLLECT>
+__global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
+{
+    constexpr int C = kListC;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const int kpad = a.kpad;
+    const uint32_t a_bytes = (uint32_t)kRowTile * kpad * 2;
+    const uint32_t b_bytes = (uint32_t)kBN * kpad * 2;
+    uint8_t *sA = smem_raw;
+    uint8_t *sB = smem_raw + a_bytes;
+    TcShared *sh = reinterpret_cast<TcShared *>(sB + (size_t)kStages * b_bytes);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = blockIdx.y;
+    const int64_t cb = a.col_begin + (int64_t)split * a.cols_per_split;
+    int64_t ce = cb + a.cols_per_split;
+    if (ce > a.col_end) ce = a.col_end;
+    const int ntiles = ce > cb ? (int)((ce - cb + kBN - 1) / kBN) : 0;
+    const int64_t slot0 = (int64_t)blockIdx.x * kRowTile;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sh->full[s], 1);
+            mbar_init(&sh->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sh->tfull[b], 1);
+            mbar_init(&sh->tempty[b], kEpiWarps);
+        }
+        mbar_init(&sh->drain, 1);
+        sh->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32(&sh->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+
+    // Row operand tile: 256 rows gathered (a row list, or consecutive rows) into the
+    // interleaved layout by the epilogue threads.
+    int myrow_slot = -1;
+    uint32_t myrow = 0, mycomp = 0;
+    if (warp < kEpiWarps) {
+        const int r = (warp >> 2) * 128 + (warp & 3) * 32 + lane;   // row within the tile
+        const int64_t slot = slot0 + r;
+        const int chunks = kpad >> 3;
+        uint4 *dst = reinterpret_cast<uint4 *>(sA);
+        if (slot < a.nslots) {
+            myrow_slot = r;
+            myrow = a.rows ? a.rows[slot] : (uint32_t)slot;
+            mycomp = a.comp ? a.comp[myrow] : 0u;
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.XA);
+            for (int c = 0; c < chunks; ++c)
+                dst[((r >> 3) * chunks + c) * 8 + (r & 7)] = src[(((int64_t)myrow >> 3) * chunks + c) * 8 + (myrow & 7)];
+        } else {
+            for (int c = 0; c < chunks; ++c) dst[((r >> 3) * chunks + c) * 8 + (r & 7)] = make_uint4(0, 0, 0, 0);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort_flag = &sh->abort_flag;
+
+    if (warp == kProdWarp) {
+        // whole warp walks the loop; lane 0 waits and issues, the result is broadcast
+        int issued = 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const int s = t % kStages;
+            int ok = 1;
+            if (lane == 0 && t >= kStages) ok = mbar_wait(&sh->empty[s], ((t / kStages) - 1) & 1, abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                *abort_flag = 1;
+                break;
+            }
+            if (lane == 0) {
+                mbar_arrive_expect_tx(&sh->full[s], b_bytes);
+                const int64_t col = cb + (int64_t)t * kBN;
+                bulk_g2s(sB + (size_t)s * b_bytes, a.XB + col * kpad, b_bytes, &sh->full[s]);
+            }
+            issued = t + 1;
+            __syncwarp();
+        }
+        // drain: every issued copy must have landed before the CTA exits
+        if (lane == 0) {
+            for (int t = issued - kStages < 0 ? 0 : issued - kStages; t < issued; ++t) {
+                const uint64_t t0 = global_ns();
+                while (!mbar_try_wait(&sh->full[t % kStages], (t / kStages) & 1) && global_ns() - t0 < kWaitNs)
+                    __nanosleep(256);
+            }
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        const uint32_t idesc = instr_desc(a.fp16);
+        const uint32_t lbo = 128, sbo = (uint32_t)(kpad / 8) * 128;
+        const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB);
+        const int ksteps = kpad / 16;
+        int done = 0;
+        for (int t = 0; t < ntiles; ++t) {
+            const int s = t % kStages, b = t & 1;
+            int ok = 1;
+            if (lane == 0) {
+                ok = mbar_wait(&sh->full[s], (t / kStages) & 1, abort_flag);
+                if (ok && t >= 2) ok = mbar_wait(&sh->tempty[b], ((t >> 1) - 1) & 1, abort_flag);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            if (lane == 0) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t d_tmem = tmem + (uint32_t)((b * 2 + h) * kBN);
+                    for (int kk = 0; kk < ksteps; ++kk) {
+                        uint64_t ad = smem_desc(aaddr + (uint32_t)h * 16u * sbo + (uint32_t)kk * 256u, lbo, sbo);
+                        uint64_t bd = smem_desc(baddr + (uint32_t)s * b_bytes + (uint32_t)kk * 256u, lbo, sbo);
+                        mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    }
+                }
+                mma_commit(&sh->empty[s]);
+                mma_commit(&sh->tfull[b]);
+            }
+            done = t + 1;
+            __syncwarp();
+        }
+        // every issued MMA completes before TMEM is freed
+        if (lane == 0 && done > 0) {
+            mma_commit(&sh->drain);
+            const uint64_t t0 = global_ns();
+            while (!mbar_try_wait(&sh->drain, 0) && global_ns() - t0 < kWaitNs) __nanosleep(256);
+        }
+        __syncwarp();
+    } else {
+        // epilogue
+        const int half = warp >> 2, quad = warp & 3;
+        float thr = -INFINITY;
+        if (myrow_slot >= 0) thr = COLLECT ? a.thr[slot0 + myrow_slot] : INFINITY;
+        float lv[C];
+        uint32_t lj[C];
+        if (!COLLECT) {
+#pragma unroll
+            for (int m = 0; m < C; ++m) {
+                lv[m] = INFINITY;
+                lj[m] = kInvalid;
+            }
+        }
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        float *scratch = reinterpret_cast<float *>(sh + 1) + threadIdx.x;   // [32][256], own column
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t & 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(&sh->tfull[b], (t >> 1) & 1, abort_flag);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int64_t col0 = cb + (int64_t)t * kBN;
+#pragma unroll 1
+            for (int ch = 0; ch < kBN / 32; ++ch) {
+                uint32_t v[32];
+                tmem_ld32(lane_base + (uint32_t)((b * 2 + half) * kBN + ch * 32), v);
+                tmem_wait_ld();
+                float m = __uint_as_float(v[0]);
+#pragma unroll
+                for (int q = 1; q < 31; q += 2) m = min3f(m, __uint_as_float(v[q]), __uint_as_float(v[q + 1]));
+                m = fminf(m, __uint_as_float(v[31]));
+                const bool hit = COLLECT ? (m <= thr) : (m < thr);
+                if (hit) {
+                    // rare: stage the chunk in this thread's shared-memory column and walk it
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) scratch[q * kEpiWarps * 32] = __uint_as_float(v[q]);
+#pragma unroll 1
+                    for (int q = 0; q < 32; ++q) {
+                        const float val = scratch[q * kEpiWarps * 32];
+                        const bool pass = COLLECT ? (val <= thr) : (val < thr);
+                        if (!pass) continue;
+                        const int64_t j = col0 + ch * 32 + q;
+                        if (j >= ce || (uint32_t)j == myrow) continue;
+                        if (a.comp && a.comp[j] == mycomp) continue;
+                        if (COLLECT) {
+                            const int64_t sl = slot0 + myrow_slot;
+                            uint32_t p = atomicAdd(&a.coll_cnt[sl], 1u);
+                            if ((int64_t)p < a.coll_cap) a.coll_j[sl * a.coll_cap + p] = (uint32_t)j;
+                        } else {
+                            list_insert<C>(lv, lj, val, (uint32_t)j);
+                            thr = lv[C - 1];
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sh->tempty[b]);
+        }
+        if (!COLLECT && myrow_slot >= 0) {
+            const int64_t base = ((slot0 + myrow_slot) * a.splits + split) * C;
+#pragma unroll
+            for (int m = 0; m < C; ++m) {
+                a.out_v[base + m] = lv[m];
+                a.out_j[base + m] = lj[m];
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && sh->abort_flag) atomicExch(a.err_flag, 1);
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
+}  // namespace
+
+size_t sweep_tc_smem_bytes(int kpad)
+{
+    size_t need = (size_t)kRowTile * kpad * 2 + (size_t)kStages * kBN * kpad * 2 + sizeof(TcShared) +
+                  (size_t)32 * kEpiWarps * 32 * sizeof(float) + 1024;
+    // at least ~half of the SM's shared memory: one CTA per SM (it holds all of TMEM)
+    const size_t one_per_sm = 120 * 1024;
+    return need > one_per_sm ? need : one_per_sm;
+}
+
+cudaError_t launch_sweep_tc(const SweepArgs &a, bool collect, cudaStream_t s)
+{
+    const size_t smem = sweep_tc_smem_bytes(a.kpad);
+    dim3 grid((unsigned)((a.nslots + kRowTile - 1) / kRowTile), (unsigned)a.splits);
+    cudaError_t e;
+    if (collect) {
+        e = cudaFuncSetAttribute(k_sweep_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sweep_tc<true><<<grid, kThreadsTc, smem, s>>>(a);
+        count_launches(1);
+    } else {
+        e = cudaFuncSetAttribute(k_sweep_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sweep_tc<false><<<grid, kThreadsTc, smem, s>>>(a);
+        count_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace nnm

@@ -1,0 +1,71 @@
+"""The C ABI library builds for sm_103a, loads without a GPU, and exports every
+function include/nnm.h declares with the struct layouts the binding assumes."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nnm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nnm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1402_3789_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert set(names) == {"nnm_create", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats",
+                          "nnm_last_error", "nnm_status_string", "nnm_destroy"}
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_1402_3789_gb300 import nnm
+    assert set(nnm.EXPORTS) == set(names)
+
+
+def test_status_strings_without_gpu(lib):
+    lib.nnm_status_string.restype = ctypes.c_char_p
+    assert lib.nnm_status_string(0) == b"NNM_OK"
+    assert lib.nnm_status_string(5) == b"NNM_ETIMEOUT"
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    P = ctypes.c_void_p
+    lib.nnm_create.argtypes = [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_int, P, P, ctypes.POINTER(P)]
+    out = P(1)
+    dummy = P(16)
+    assert lib.nnm_create(dummy, 0, 8, 0, 0, None, None, ctypes.byref(out)) == 1      # N < 1
+    assert out.value is None
+    assert lib.nnm_create(dummy, 10, 33, 0, 0, None, None, ctypes.byref(out)) == 1    # d > 32
+    assert lib.nnm_create(dummy, 10, 0, 0, 0, None, None, ctypes.byref(out)) == 1     # d < 1
+    assert lib.nnm_create(None, 10, 4, 0, 0, None, None, ctypes.byref(out)) == 1      # null X
+    assert lib.nnm_create(dummy, 1 << 31, 4, 0, 0, None, None, ctypes.byref(out)) == 1
+    assert lib.nnm_create(dummy, 10, 4, 1, 0, None, None, ctypes.byref(out)) == 6     # metric
+    assert lib.nnm_create(dummy, 10, 4, 0, 3, None, None, ctypes.byref(out)) == 6     # precision
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    from paper_1402_3789_gb300 import nnm
+    prog = tmp_path / "sizes.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "nnm.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(nnm_merge), sizeof(nnm_edge),'
+                    ' sizeof(nnm_restrictions), sizeof(nnm_options), sizeof(nnm_stats),'
+                    ' offsetof(nnm_stats, max_abs_err), offsetof(nnm_stats, scale)); return 0;}\n')
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [nnm.MERGE_DTYPE.itemsize, nnm.EDGE_DTYPE.itemsize, ctypes.sizeof(nnm.nnm_restrictions),
+            ctypes.sizeof(nnm.nnm_options), ctypes.sizeof(nnm.nnm_stats),
+            nnm.nnm_stats.max_abs_err.offset, nnm.nnm_stats.scale.offset]
+    assert got == want

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Exact results (indices, binary64 distances, merge tree, merges, labels) must be equal
+element by element: every decision of the method is taken on the canonical binary64
+squared distance with the (D, min, max) tie-break, which both sides compute the same
+way.  Inputs are the seeded mixtures of paper_1402_3789_gb300.inputs at sizes that span
+several row tiles (256 rows) and column tiles, with ragged tails.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+PRECISIONS = ["fp32", "bf16", "fp16"]
+
+
+@pytest.fixture(scope="module")
+def nnm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1402_3789_gb300 import build, nnm as binding
+    build.build()
+    binding.load_library()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def make(name, n, seed=None):
+    from paper_1402_3789_gb300.inputs import make as mk
+    return mk(name, n=n, seed=seed)
+
+
+def dev(X):
+    return torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+
+
+def run_nearest(nnm, X, k, precision, **opt):
+    ctx = nnm.nnm_create(dev(X), precision=precision, **opt)
+    try:
+        idx, D = nnm.nnm_nearest(ctx, k)
+        return idx.cpu().numpy().view(np.uint32), D.cpu().numpy(), nnm.nnm_get_stats(ctx)
+    finally:
+        nnm.nnm_destroy(ctx)
+
+
+def run_cluster(nnm, X, restr, precision, **opt):
+    ctx = nnm.nnm_create(dev(X), precision=precision, **opt)
+    try:
+        res = nnm.nnm_cluster(ctx, restr)
+        tree = nnm.nnm_get_tree(ctx)
+        return tree, res.merges(), res.labels.cpu().numpy(), res.n_clusters, nnm.nnm_get_stats(ctx)
+    finally:
+        nnm.nnm_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------------
+# nearest neighbours
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("n,d,k", [(4096, 8, 1), (4096, 8, 8), (3001, 25, 5), (777, 3, 24), (300, 32, 2),
+                                   (1000, 1, 4), (5000, 16, 12)])
+def test_nearest_matches_oracle(nnm, orc, precision, n, d, k):
+    rng = np.random.default_rng(n + d)
+    X = (rng.standard_normal((n, d)) * rng.uniform(0.5, 3, d) + rng.integers(0, 5, (n, 1))).astype(np.float32)
+    idx, D, st = run_nearest(nnm, X, k, precision)
+    oi, oD = orc.knn(X, k)
+    assert np.array_equal(idx, oi)
+    assert np.array_equal(D, oD)
+    if precision == "fp32":
+        assert st["max_rel_err"] <= (d + 2) * 2.0 ** -24 * 1.01
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_nearest_paper_mixture_small(nnm, orc, precision):
+    X = make("nnm_n4096_d8", 4096)
+    idx, D, _ = run_nearest(nnm, X, 4, precision)
+    oi, oD = orc.knn(X, 4)
+    assert np.array_equal(idx, oi) and np.array_equal(D, oD)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_nearest_ties_and_duplicates(nnm, orc, precision):
+    # the tie-stress recipe (1/64 grid, 2% duplicates) at a small size: many equal D
+    X = make("nnm_n1048576_d25_ties", 6000)
+    idx, D, st = run_nearest(nnm, X, 6, precision)
+    oi, oD = orc.knn(X, 6)
+    assert np.array_equal(idx, oi) and np.array_equal(D, oD)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_nearest_all_identical_rows(nnm, orc, precision):
+    X = np.ones((700, 5), dtype=np.float32) * 3.25
+    idx, D, _ = run_nearest(nnm, X, 3, precision)
+    oi, oD = orc.knn(X, 3)
+    assert np.array_equal(idx, oi) and np.array_equal(D, oD)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_nearest_large_offset_and_spread(nnm, orc, precision):
+    # large common offset (removed by centring) and features of very different scale:
+    # the rounding radii are large, so the completeness test does real work
+    rng = np.random.default_rng(3)
+    X = (1000.0 + rng.standard_normal((3000, 12)) * np.geomspace(1e-3, 30, 12)).astype(np.float32)
+    idx, D, st = run_nearest(nnm, X, 5, precision)
+    oi, oD = orc.knn(X, 5)
+    assert np.array_equal(idx, oi) and np.array_equal(D, oD)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_nearest_forced_column_splits(nnm, orc, precision):
+    X = make("nnm_n262144_d16", 9000)
+    for s in (1, 3, 7):
+        idx, D, _ = run_nearest(nnm, X, 3, precision, col_split=s)
+        oi, oD = orc.knn(X, 3)
+        assert np.array_equal(idx, oi) and np.array_equal(D, oD)
+
+
+# ----------------------------------------------------------------------------------
+# merge tree, restrictions, labels
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_cluster_full_tree_n4096(nnm, orc, precision):
+    X = make("nnm_n4096_d8", 4096)
+    tree, merges, labels, K, st = run_cluster(nnm, X, None, precision)
+    otree, omerges, olabels, oK = orc.cluster(X, None)
+    assert np.array_equal(tree, otree)
+    assert np.array_equal(merges, omerges)
+    assert K == oK == 1
+    assert np.array_equal(labels, olabels)
+
+
+RESTRICTIONS = [
+    {"max_join_dist": 0.8},
+    {"kl1_stop_clusters": 37},
+    {"max_join_dist": 1.0, "kl1_stop_clusters": 20},
+    {"kl2_max_pre_size": 40},
+    {"kl3_max_size": 100, "max_join_dist": 1.3},
+    {"kl4_min_size": 6, "kl3_max_size": 200},
+    {"kl4_min_size": 12, "kl1_stop_clusters": 50, "kl2_max_pre_size": 30, "kl3_max_size": 90},
+]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("restr", RESTRICTIONS, ids=[str(i) for i in range(len(RESTRICTIONS))])
+def test_cluster_restrictions(nnm, orc, precision, restr):
+    X = make("nnm_n4096_d8", 5000, seed=11)
+    tree, merges, labels, K, _ = run_cluster(nnm, X, restr, precision)
+    otree, omerges, olabels, oK = orc.cluster(X, restr)
+    assert np.array_equal(tree, otree)
+    assert np.array_equal(merges, omerges)
+    assert K == oK
+    assert np.array_equal(labels, olabels)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_cluster_ties_tree(nnm, orc, precision):
+    X = make("nnm_n1048576_d25_ties", 3000)
+    tree, merges, labels, K, _ = run_cluster(nnm, X, {"max_join_dist": 0.5}, precision)
+    otree, omerges, olabels, oK = orc.cluster(X, {"max_join_dist": 0.5})
+    assert np.array_equal(tree, otree)
+    assert np.array_equal(merges, omerges) and K == oK and np.array_equal(labels, olabels)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_cluster_ragged_and_tiny(nnm, orc, precision):
+    rng = np.random.default_rng(5)
+    for n, d in ((2, 3), (3, 1), (257, 7), (1023, 25), (2049, 2)):
+        X = rng.standard_normal((n, d)).astype(np.float32)
+        tree, merges, labels, K, _ = run_cluster(nnm, X, None, precision)
+        otree, omerges, olabels, oK = orc.cluster(X, None)
+        assert np.array_equal(tree, otree), (n, d)
+        assert np.array_equal(merges, omerges) and K == oK and np.array_equal(labels, olabels)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_cluster_freeze_at_cap_keeps_the_restricted_result(nnm, orc, precision):
+    X = make("nnm_n262144_d16", 8000)
+    restr = {"max_join_dist": 1.5, "kl1_stop_clusters": 200}
+    tree, merges, labels, K, _ = run_cluster(nnm, X, restr, precision, freeze_at_cap=True)
+    otree, omerges, olabels, oK = orc.cluster(X, restr)
+    assert np.array_equal(merges, omerges) and K == oK and np.array_equal(labels, olabels)
+    cut = otree[otree["D"] <= 1.5 * 1.5]
+    assert np.array_equal(np.sort(tree[tree["D"] <= 2.25], order=["D", "a", "b"]), cut)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_cluster_mixture_n20000(nnm, orc, precision):
+    X = make("nnm_n262144_d16", 20000)
+    restr = {"max_join_dist": 1.5, "kl1_stop_clusters": 200}
+    tree, merges, labels, K, st = run_cluster(nnm, X, restr, precision)
+    otree, omerges, olabels, oK = orc.cluster(X, restr)
+    assert np.array_equal(tree, otree)
+    assert np.array_equal(merges, omerges) and K == oK and np.array_equal(labels, olabels)
+
+
+# ----------------------------------------------------------------------------------
+# errors
+# ----------------------------------------------------------------------------------
+
+def test_errors(nnm):
+    X = np.random.default_rng(0).standard_normal((100, 4)).astype(np.float32)
+    Xbad = X.copy()
+    Xbad[7, 2] = np.nan
+    with pytest.raises(nnm.NNMError) as e:
+        nnm.nnm_create(dev(Xbad))
+    assert e.value.status == nnm.NNM_ENONFINITE
+    Xbad[7, 2] = np.inf
+    with pytest.raises(nnm.NNMError):
+        nnm.nnm_create(dev(Xbad))
+    ctx = nnm.nnm_create(dev(X))
+    try:
+        for k in (0, 25, 100):
+            with pytest.raises(nnm.NNMError) as e:
+                nnm.nnm_nearest(ctx, k)
+            assert e.value.status == nnm.NNM_EINVAL
+        with pytest.raises(nnm.NNMError) as e:
+            nnm.nnm_cluster(ctx, {"kl2_max_pre_size": 10, "kl3_max_size": 10})
+        assert e.value.status == nnm.NNM_EINVAL
+        with pytest.raises(nnm.NNMError) as e:
+            nnm.nnm_cluster(ctx, {"kl1_stop_clusters": -1})
+        assert e.value.status == nnm.NNM_EINVAL
+        with pytest.raises(nnm.NNMError) as e:
+            nnm.nnm_cluster(ctx, {"semantics": 1})
+        assert e.value.status == nnm.NNM_EUNSUPPORTED
+        # the context stays usable after rejected calls
+        idx, D = nnm.nnm_nearest(ctx, 2)
+        assert idx.shape == (100, 2)
+    finally:
+        nnm.nnm_destroy(ctx)
