@@ -159,7 +159,7 @@ nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metri
 /* nnm_nearest -- exact k nearest neighbours of every row (self excluded), in order
  * of (D, index): the per-row minima of the second and third parallel items of
  * "Overall idea of the algorithm" (all pairwise distances, minimum selection).
- *   k        1 <= k <= 24 and k < N (EINVAL otherwise).
+ *   k        1 <= k <= 16 and k < N (EINVAL otherwise).
  *   idx_dev  uint32 [N][k] device, written.   D_dev  float64 [N][k] device, written. */
 nnm_status nnm_nearest(nnm_ctx *ctx, int32_t k, uint32_t *idx_dev, double *D_dev);
 

@@ -22,8 +22,9 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = [
     ("nnm_api", "nnm_api.cu", []),
     ("prep", "prep.cu", []),
-    ("sweep_fp32_lo", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_LO"]),
-    ("sweep_fp32_hi", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_HI"]),
+    ("sweep_fp32_a", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_A"]),
+    ("sweep_fp32_b", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_B"]),
+    ("sweep_fp32_c", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_C"]),
     ("sweep_tc", "sweep_tc.cu", []),
     ("rerank", "rerank.cu", []),
     ("rounds", "rounds.cu", []),

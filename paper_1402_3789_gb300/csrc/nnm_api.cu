@@ -42,6 +42,7 @@ struct nnm_ctx {
     int fp16 = 0;
     double scale = 1.0;
     Margin margin{};
+    SelConst selc{};
     // operands
     float *Xs = nullptr;
     uint16_t *XA = nullptr, *XB = nullptr;
@@ -49,7 +50,8 @@ struct nnm_ctx {
     // sweep / re-rank scratch
     float *cand_v = nullptr;
     uint32_t *cand_j = nullptr;
-    size_t cand_cap = 0;         // entries
+    uint8_t *cand_ovf = nullptr;
+    size_t cand_cap = 0;         // records (one per row slot and column range)
     uint32_t *ovf_row = nullptr;
     float *ovf_thr = nullptr;
     size_t ovf_cap = 0;          // slots
@@ -177,13 +179,37 @@ int choose_splits(const nnm_ctx *c, int64_t nslots)
     return (int)s;
 }
 
-nnm_status ensure_cand(nnm_ctx *c, size_t entries)
+nnm_status ensure_cand(nnm_ctx *c, size_t records)
 {
-    if (entries <= c->cand_cap) return NNM_OK;
-    NNM_TRY(dalloc(c, &c->cand_v, entries));
-    NNM_TRY(dalloc(c, &c->cand_j, entries));
-    c->cand_cap = entries;
+    if (records <= c->cand_cap) return NNM_OK;
+    NNM_TRY(dalloc(c, &c->cand_v, records * kListC));
+    NNM_TRY(dalloc(c, &c->cand_j, records * kListC));
+    NNM_TRY(dalloc(c, &c->cand_ovf, records));
+    c->cand_cap = records;
     return NNM_OK;
+}
+
+// float >= x (round up)
+float up_f(double x)
+{
+    float f = (float)x;
+    if ((double)f < x) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// Host side of the sweeps' pruning constants (FP32, rounded up, enlarged by 2^-20).
+SelConst make_selconst(const Margin &m)
+{
+    SelConst sc{};
+    const double grow = 1.0 + 0x1p-20;
+    sc.tensor = m.tensor;
+    sc.c1 = up_f((1.0 + m.gamma) / (1.0 - m.gamma) * grow * grow);
+    sc.c0 = up_f(m.alpha * grow + 1e-37);
+    sc.gamma = up_f(m.gamma * grow);
+    sc.R = up_f(m.R * grow);
+    sc.Pmax = up_f(m.Pmax * grow);
+    sc.Emax = up_f(m.Emax * grow);
+    return sc;
 }
 
 nnm_status ensure_ovf(nnm_ctx *c, size_t slots)
@@ -218,6 +244,9 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.col_begin = 0;
     a.col_end = c->N;
     a.err_flag = &c->derr[0];
+    a.m = c->margin;
+    a.sc = c->selc;
+    a.kc = 1;
     return a;
 }
 
@@ -253,7 +282,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     const int S = choose_splits(c, nslots);
     const int64_t cps = round_up((c->N + S - 1) / S, 128);
     const int splits = (int)((c->N + cps - 1) / cps);
-    NNM_TRY(ensure_cand(c, (size_t)nslots * splits * kListC));
+    NNM_TRY(ensure_cand(c, (size_t)nslots * splits));
     NNM_TRY(ensure_ovf(c, (size_t)nslots));
 
     SweepArgs sa = base_sweep(c);
@@ -264,6 +293,8 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     sa.splits = splits;
     sa.out_v = c->cand_v;
     sa.out_j = c->cand_j;
+    sa.out_ovf = c->cand_ovf;
+    sa.kc = k;
     {
         Phase ph(c, &c->stats.ms_sweep);
         if (full) NNM_CUDA(c, cudaEventRecord(c->ev0, c->stream));
@@ -291,6 +322,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
         fa.splits = splits;
         fa.in_v = c->cand_v;
         fa.in_j = c->cand_j;
+        fa.in_ovf = c->cand_ovf;
         fa.k = k;
         fa.m = c->margin;
         fa.res_j = res_j;
@@ -466,6 +498,7 @@ nnm_status prepare(nnm_ctx *c)
         c->stats.k_pad = c->kpad;
         c->stats.scale = c->scale;
     }
+    c->selc = make_selconst(c->margin);
     return NNM_OK;
 }
 
@@ -650,7 +683,7 @@ nnm_status nnm_nearest(nnm_ctx *c, int32_t k, uint32_t *idx_dev, double *D_dev)
     c->err.clear();
     c->status = NNM_OK;
     if (!idx_dev || !D_dev) return fail(c, NNM_EINVAL, "null output buffer");
-    if (k < 1 || k > kMaxK || (int64_t)k >= c->N) return fail(c, NNM_EINVAL, "k=%d outside 1..min(24, N-1)", k);
+    if (k < 1 || k > kMaxK || (int64_t)k >= c->N) return fail(c, NNM_EINVAL, "k=%d outside 1..min(16, N-1)", k);
     reset_stats(c);
     {
         Phase total(c, &c->stats.ms_total);
@@ -757,6 +790,7 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->E);
     dfree(c->cand_v);
     dfree(c->cand_j);
+    dfree(c->cand_ovf);
     dfree(c->ovf_row);
     dfree(c->ovf_thr);
     dfree(c->coll_cnt);

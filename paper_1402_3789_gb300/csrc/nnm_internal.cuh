@@ -16,11 +16,33 @@ void count_launches(int n);
 int64_t launches_so_far();
 
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
-constexpr int kListC = 32;        // candidates a sweep keeps per (row, column range)
-constexpr int kMaxK = 24;         // largest k of nnm_nearest / cache width
+constexpr int kListC = 48;        // record slots per (row, column range): 16 top + 32 band
+constexpr int kMaxK = 16;         // largest k of nnm_nearest / cache width
 constexpr int kRowTile = 256;     // rows per sweep CTA (both candidate paths)
 constexpr int kMaxSplits = 32;    // column ranges per row tile
 constexpr uint64_t kMaxKey = 0xFFFFFFFFFFFFFFFFull;
+
+struct Margin {
+    int tensor;         // 0: FP32 direct candidates; 1: tensor-core candidates
+    double gamma;       // relative error bound of one candidate value
+    double alpha;       // absolute slack (underflow)
+    double R;           // tensor: max rounding radius over rows (scaled units)
+    double Pmax;        // tensor: max |x_hat| over rows
+    double Emax;        // tensor: max norm-split error over rows
+    double inv_scale2;  // 1 / scale^2 (tensor candidates are in scaled units)
+    const float *r;     // tensor: per-row rounding radius
+    const float *P;     // tensor: per-row |x_hat|
+    const float *E;     // tensor: per-row norm-split error
+};
+
+// Per-launch constants of the sweeps' pruning threshold (an FP32 upper bound, rounded
+// up, of the re-rank's binary64 threshold T; see select.cuh and rerank.cu).
+struct SelConst {
+    int tensor;
+    float c1, c0;   // FP32 path: T = (v + c0) * c1 + c0
+    float gamma;    // tensor path: accumulation bound
+    float R, Pmax, Emax;
+};
 
 // ---------------------------------------------------------------------------------
 // Candidate sweep (K1 FP32 direct / K2 tensor core): for each row slot, either keep
@@ -44,9 +66,14 @@ struct SweepArgs {
     // columns
     int64_t col_begin, col_end, cols_per_split;
     int splits;
-    // top-C output: [nslots][splits][kListC]
+    // selection
+    int kc;                   // the re-rank needs the kc smallest (1..16)
+    Margin m;                 // per-row bound arrays (tensor path)
+    SelConst sc;
+    // top-C output: [nslots][splits][kListC] records and [nslots][splits] overflow flags
     float *out_v;
     uint32_t *out_j;
+    uint8_t *out_ovf;
     // collect mode
     const float *thr;         // per slot, values <= thr are appended
     uint32_t *coll_cnt;       // per slot counters
@@ -65,19 +92,6 @@ size_t sweep_tc_smem_bytes(int kpad);
 // ---------------------------------------------------------------------------------
 // Exact re-rank (K3)
 // ---------------------------------------------------------------------------------
-struct Margin {
-    int tensor;         // 0: FP32 direct candidates; 1: tensor-core candidates
-    double gamma;       // relative error bound of one candidate value
-    double alpha;       // absolute slack (underflow)
-    double R;           // tensor: max rounding radius over rows (scaled units)
-    double Pmax;        // tensor: max |x_hat| over rows
-    double Emax;        // tensor: max norm-split error over rows
-    double inv_scale2;  // 1 / scale^2 (tensor candidates are in scaled units)
-    const float *r;     // tensor: per-row rounding radius
-    const float *P;     // tensor: per-row |x_hat|
-    const float *E;     // tensor: per-row norm-split error
-};
-
 struct FinalizeArgs {
     const float *X;            // user's rows [N][d]
     int d;
@@ -87,6 +101,7 @@ struct FinalizeArgs {
     int splits;
     const float *in_v;         // [nslots][splits][kListC]
     const uint32_t *in_j;
+    const uint8_t *in_ovf;     // [nslots][splits]
     int k;                     // results per row
     Margin m;
     // results (indexed by row)

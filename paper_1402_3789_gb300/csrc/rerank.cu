@@ -8,9 +8,10 @@
 // every operation IEEE binary64 round-to-nearest without contraction, and the k
 // smallest (D, j) are kept.  Completeness: a candidate value v approximates the exact
 // squared distance within a proven bound; from the k-th smallest v the re-rank derives a
-// threshold T such that every column of the exact top k has v <= T.  If a column range
-// kept kListC values all <= T, values above may have been dropped, and the row goes to
-// the collect pass instead (every eligible column with v <= T).
+// threshold T such that every column of the exact top k has v <= T.  Each column range
+// of the sweep kept every eligible value <= its own running bound, which is >= T,
+// unless its band overflowed; a row with an overflowed range goes to the collect pass
+// (every eligible column with v <= T) instead.
 #include "nnm_internal.cuh"
 
 namespace nnm {
@@ -119,40 +120,32 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     const float *vin = a.in_v + q * n_ent;
     const uint32_t *jin = a.in_j + q * n_ent;
     for (int e = lane; e < n_ent; e += 32) {
-        wv[e] = vin[e];
-        wj[e] = jin[e];
+        const uint32_t j = jin[e];
+        const float v = vin[e];
+        wv[e] = v;
+        wj[e] = j;
+        wD[e] = j != kInvalid ? (double)v : INFINITY;
     }
+    const bool ovf = lane < a.splits && a.in_ovf[q * a.splits + lane];
     __syncwarp();
-    // valid entries per column range (lists are sorted, invalid ones at the end)
-    int cnt = 0;
-    if (lane < a.splits)
-        for (int m = 0; m < kListC; ++m) cnt += wj[lane * kListC + m] != kInvalid;
-    // k-th smallest value over all ranges: k-way merge of the sorted lists
-    int head = 0, taken = 0;
-    float vk = INFINITY;
+    // k-th smallest value over all records (extraction on a scratch copy)
+    int taken = 0;
+    double vk = INFINITY;
     for (int m = 0; m < a.k; ++m) {
-        float hv = (lane < a.splits && head < cnt) ? wv[lane * kListC + head] : INFINITY;
-        int hl = lane;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float ov = __shfl_xor_sync(0xffffffffu, hv, o);
-            int ol = __shfl_xor_sync(0xffffffffu, hl, o);
-            if (ov < hv || (ov == hv && ol < hl)) {
-                hv = ov;
-                hl = ol;
-            }
-        }
-        if (!(hv < INFINITY)) break;
-        vk = hv;
+        Best b = {INFINITY, kInvalid, -1};
+        for (int e = lane; e < n_ent; e += 32)
+            if (wD[e] < INFINITY && less_dj(wD[e], (uint32_t)e, b.D, b.j)) b = {wD[e], (uint32_t)e, e};
+        b = warp_min(b);
+        if (b.e < 0) break;
+        vk = b.D;
         ++taken;
-        if (lane == hl) ++head;
+        if (lane == 0) wD[b.e] = INFINITY;
+        __syncwarp();
     }
-    const double T = threshold(a.m, i, taken < a.k ? INFINITY : vk);
-    const bool ok = lane >= a.splits || cnt < kListC || (double)wv[lane * kListC + kListC - 1] > T;
-    const int total = __reduce_add_sync(0xffffffffu, lane < a.splits ? cnt : 0);
-    if (!__all_sync(0xffffffffu, ok)) {
+    const double T = threshold(a.m, i, taken < a.k ? INFINITY : (float)vk);
+    if (__any_sync(0xffffffffu, ovf)) {
         if (lane == 0) {
-            uint32_t p = atomicAdd(a.ovf_cnt, 1u);
+            const uint32_t p = atomicAdd(a.ovf_cnt, 1u);
             a.ovf_row[p] = i;
             a.ovf_thr[p] = __double2float_ru(T);
         }
@@ -184,7 +177,8 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     }
     if (lane == 0) {
         if (a.res_n) a.res_n[i] = (uint8_t)n_out;
-        if (a.res_exh) a.res_exh[i] = (uint8_t)(total <= a.k);
+        // fewer than k results means every eligible column was among the candidates
+        if (a.res_exh) a.res_exh[i] = (uint8_t)(n_out < a.k);
         atomic_max_nonneg(a.st_max_abs, emax_abs);
         atomic_max_nonneg(a.st_max_rel, emax_rel);
         if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nc);
@@ -224,7 +218,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s)
 {
     if (a.nslots <= 0) return cudaSuccess;
-    const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4);
+    const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4);   // <= 96 KB
     cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((a.nslots + kFinWarps - 1) / kFinWarps);

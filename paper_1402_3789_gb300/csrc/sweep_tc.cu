@@ -17,7 +17,7 @@
 // TMEM: 512 columns = 2 accumulator buffers x 2 row halves x 128 columns (fp32).
 // Every wait is bounded (global timer); on time-out the CTA raises the error flag,
 // drains its own copies and MMAs with bounded waits, frees TMEM and exits.
-#include "nnm_internal.cuh"
+#include "select.cuh"
 
 namespace nnm {
 
@@ -28,7 +28,8 @@ constexpr int kThreadsTc = (kEpiWarps + 2) * 32;
 constexpr int kMmaWarp = 8;
 constexpr int kProdWarp = 9;
 constexpr int kBN = 128;          // columns per B tile
-constexpr int kStages = 8;
+constexpr int kMaxStages = 8;
+constexpr int kStageStride = 36;   // floats per thread in the hit-staging area (16-byte rows, no bank conflicts)
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -149,7 +150,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
         : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Wait for this thread's tcgen05.ld results.  The 32 registers are tied to the wait as
+// read-write operands so that no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+          "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]),
+          "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+          "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+        :
+        : "memory");
+}
+
+// Order-only barrier for 32 more registers after a wait (asm volatile keeps the order).
+__device__ __forceinline__ void reg_fence(uint32_t (&v)[32])
+{
+    asm volatile(""
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                   "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]),
+                   "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]),
+                   "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
 
 __device__ __forceinline__ float min3f(float a, float b, float c)
 {
@@ -158,24 +184,9 @@ __device__ __forceinline__ float min3f(float a, float b, float c)
     return r;
 }
 
-template <int C>
-__device__ __forceinline__ void list_insert(float (&lv)[C], uint32_t (&lj)[C], float v, uint32_t j)
-{
-#pragma unroll
-    for (int m = 0; m < C; ++m) {
-        bool sw = v < lv[m];
-        float tv = sw ? lv[m] : v;
-        uint32_t tj = sw ? lj[m] : j;
-        lv[m] = sw ? v : lv[m];
-        lj[m] = sw ? j : lj[m];
-        v = tv;
-        j = tj;
-    }
-}
-
 struct __align__(8) TcShared {
-    uint64_t full[kStages];
-    uint64_t empty[kStages];
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
     uint64_t drain;
@@ -183,17 +194,30 @@ struct __align__(8) TcShared {
     int abort_flag;
 };
 
-template <bool COLLECT>
+// Shared-memory stages of the B ring that fit next to the other regions.
+__host__ __device__ inline int tc_stages(int kpad)
+{
+    const size_t fixed = (size_t)kRowTile * kpad * 2 + 256 + (size_t)kBand * kRowTile * 8 +
+                         (size_t)kRowTile * kStageStride * 4 + 1024;
+    const size_t per = (size_t)kBN * kpad * 2;
+    int s = (int)((225 * 1024 - fixed) / per);
+    return s > kMaxStages ? kMaxStages : s;
+}
+
+template <int KC, bool COLLECT>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
 {
-    constexpr int C = kListC;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const int kpad = a.kpad;
+    const int kStages = tc_stages(kpad);
     const uint32_t a_bytes = (uint32_t)kRowTile * kpad * 2;
     const uint32_t b_bytes = (uint32_t)kBN * kpad * 2;
     uint8_t *sA = smem_raw;
     uint8_t *sB = smem_raw + a_bytes;
     TcShared *sh = reinterpret_cast<TcShared *>(sB + (size_t)kStages * b_bytes);
+    float *band_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(sh) + 256);   // [kBand][256]
+    uint32_t *band_j = reinterpret_cast<uint32_t *>(band_v + kBand * kRowTile);
+    float *stage_v = reinterpret_cast<float *>(band_j + kBand * kRowTile);               // [256][kStageStride]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
@@ -322,21 +346,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         }
         __syncwarp();
     } else {
-        // epilogue
+        // epilogue: one row per thread, 128 columns per tile in two halves of 64
         const int half = warp >> 2, quad = warp & 3;
-        float thr = -INFINITY;
-        if (myrow_slot >= 0) thr = COLLECT ? a.thr[slot0 + myrow_slot] : INFINITY;
-        float lv[C];
-        uint32_t lj[C];
-        if (!COLLECT) {
-#pragma unroll
-            for (int m = 0; m < C; ++m) {
-                lv[m] = INFINITY;
-                lj[m] = kInvalid;
-            }
-        }
+        const bool valid = myrow_slot >= 0;
+        const float cthr = (COLLECT && valid) ? a.thr[slot0 + myrow_slot] : -INFINITY;
+        RowSel<KC> sel;
+        sel.init(valid);
+        const RowConst rc = valid ? make_rowconst(a.sc, a.m, myrow) : RowConst{0.f, 0.f};
+        float *bv = band_v + threadIdx.x;
+        uint32_t *bj = band_j + threadIdx.x;
+        float *stg = stage_v + threadIdx.x * kStageStride;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-        float *scratch = reinterpret_cast<float *>(sh + 1) + threadIdx.x;   // [32][256], own column
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1;
             int ok = 1;
@@ -349,34 +369,59 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             tc_fence_after();
             const int64_t col0 = cb + (int64_t)t * kBN;
 #pragma unroll 1
-            for (int ch = 0; ch < kBN / 32; ++ch) {
-                uint32_t v[32];
-                tmem_ld32(lane_base + (uint32_t)((b * 2 + half) * kBN + ch * 32), v);
-                tmem_wait_ld();
-                float m = __uint_as_float(v[0]);
+            for (int hh = 0; hh < kBN / 64; ++hh) {
+                uint32_t v[64];
+                uint32_t(&v0)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[0]);
+                uint32_t(&v1)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[32]);
+                const uint32_t taddr = lane_base + (uint32_t)((b * 2 + half) * kBN + hh * 64);
+                tmem_ld32(taddr, v0);
+                tmem_ld32(taddr + 32, v1);
+                tmem_wait_ld(v0);
+                reg_fence(v1);
+                const float thr = COLLECT ? cthr : sel.thr;
+                float mn[2];
 #pragma unroll
-                for (int q = 1; q < 31; q += 2) m = min3f(m, __uint_as_float(v[q]), __uint_as_float(v[q + 1]));
-                m = fminf(m, __uint_as_float(v[31]));
-                const bool hit = COLLECT ? (m <= thr) : (m < thr);
-                if (hit) {
-                    // rare: stage the chunk in this thread's shared-memory column and walk it
+                for (int c = 0; c < 2; ++c) {
+                    const uint32_t *w = v + c * 32;
+                    float l1[11];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) scratch[q * kEpiWarps * 32] = __uint_as_float(v[q]);
-#pragma unroll 1
-                    for (int q = 0; q < 32; ++q) {
-                        const float val = scratch[q * kEpiWarps * 32];
-                        const bool pass = COLLECT ? (val <= thr) : (val < thr);
-                        if (!pass) continue;
-                        const int64_t j = col0 + ch * 32 + q;
+                    for (int q = 0; q < 10; ++q)
+                        l1[q] = min3f(__uint_as_float(w[3 * q]), __uint_as_float(w[3 * q + 1]),
+                                      __uint_as_float(w[3 * q + 2]));
+                    l1[10] = fminf(__uint_as_float(w[30]), __uint_as_float(w[31]));
+                    const float l2a = min3f(l1[0], l1[1], l1[2]), l2b = min3f(l1[3], l1[4], l1[5]);
+                    const float l2c = min3f(l1[6], l1[7], l1[8]), l2d = fminf(l1[9], l1[10]);
+                    mn[c] = fminf(min3f(l2a, l2b, l2c), l2d);
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (!(mn[c] <= (COLLECT ? cthr : sel.thr))) continue;
+                    // rare: stage the 32 values in this thread's shared-memory row, walk the hits
+                    const uint32_t *w = v + c * 32;
+                    uint32_t mask = 0;
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4) {
+                        *reinterpret_cast<float4 *>(stg + q) =
+                            make_float4(__uint_as_float(w[q]), __uint_as_float(w[q + 1]), __uint_as_float(w[q + 2]),
+                                        __uint_as_float(w[q + 3]));
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) mask |= (__uint_as_float(w[q]) <= thr ? 1u : 0u) << q;
+                    const int64_t jbase = col0 + hh * 64 + c * 32;
+                    while (mask) {
+                        const int q = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const float val = stg[q];
+                        const int64_t j = jbase + q;
+                        if (!(val <= (COLLECT ? cthr : sel.thr))) continue;
                         if (j >= ce || (uint32_t)j == myrow) continue;
                         if (a.comp && a.comp[j] == mycomp) continue;
                         if (COLLECT) {
                             const int64_t sl = slot0 + myrow_slot;
-                            uint32_t p = atomicAdd(&a.coll_cnt[sl], 1u);
+                            const uint32_t p = atomicAdd(&a.coll_cnt[sl], 1u);
                             if ((int64_t)p < a.coll_cap) a.coll_j[sl * a.coll_cap + p] = (uint32_t)j;
                         } else {
-                            list_insert<C>(lv, lj, val, (uint32_t)j);
-                            thr = lv[C - 1];
+                            sel.insert(val, (uint32_t)j, a.sc, rc, bv, bj, kRowTile);
                         }
                     }
                 }
@@ -386,13 +431,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             __syncwarp();
             if (lane == 0) mbar_arrive(&sh->tempty[b]);
         }
-        if (!COLLECT && myrow_slot >= 0) {
-            const int64_t base = ((slot0 + myrow_slot) * a.splits + split) * C;
-#pragma unroll
-            for (int m = 0; m < C; ++m) {
-                a.out_v[base + m] = lv[m];
-                a.out_j[base + m] = lj[m];
-            }
+        if (!COLLECT && valid) {
+            const int64_t rec = (slot0 + myrow_slot) * a.splits + split;
+            sel.write(a.out_v + rec * kListC, a.out_j + rec * kListC, a.out_ovf + rec, bv, bj, kRowTile);
         }
     }
 
@@ -409,30 +450,33 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
 
 size_t sweep_tc_smem_bytes(int kpad)
 {
-    size_t need = (size_t)kRowTile * kpad * 2 + (size_t)kStages * kBN * kpad * 2 + sizeof(TcShared) +
-                  (size_t)32 * kEpiWarps * 32 * sizeof(float) + 1024;
-    // at least ~half of the SM's shared memory: one CTA per SM (it holds all of TMEM)
+    // at least ~half of the SM's shared memory keeps one CTA per SM (it holds all of TMEM)
+    const size_t need = (size_t)kRowTile * kpad * 2 + (size_t)tc_stages(kpad) * kBN * kpad * 2 + 256 +
+                        (size_t)kBand * kRowTile * 8 + (size_t)kRowTile * kStageStride * 4 + 1024;
     const size_t one_per_sm = 120 * 1024;
     return need > one_per_sm ? need : one_per_sm;
+}
+
+template <int KC, bool COLL>
+static cudaError_t go_tc(const SweepArgs &a, dim3 grid, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_tc<KC, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_sweep_tc<KC, COLL><<<grid, kThreadsTc, smem, s>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sweep_tc(const SweepArgs &a, bool collect, cudaStream_t s)
 {
     const size_t smem = sweep_tc_smem_bytes(a.kpad);
     dim3 grid((unsigned)((a.nslots + kRowTile - 1) / kRowTile), (unsigned)a.splits);
-    cudaError_t e;
-    if (collect) {
-        e = cudaFuncSetAttribute(k_sweep_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_sweep_tc<true><<<grid, kThreadsTc, smem, s>>>(a);
-        count_launches(1);
-    } else {
-        e = cudaFuncSetAttribute(k_sweep_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_sweep_tc<false><<<grid, kThreadsTc, smem, s>>>(a);
-        count_launches(1);
-    }
-    return cudaGetLastError();
+    if (collect) return go_tc<1, true>(a, grid, smem, s);
+    if (a.kc <= 1) return go_tc<1, false>(a, grid, smem, s);
+    if (a.kc <= 2) return go_tc<2, false>(a, grid, smem, s);
+    if (a.kc <= 4) return go_tc<4, false>(a, grid, smem, s);
+    if (a.kc <= 8) return go_tc<8, false>(a, grid, smem, s);
+    return go_tc<16, false>(a, grid, smem, s);
 }
 
 }  // namespace nnm
