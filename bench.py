@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="override N (smaller runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--compare", default="", help="comma list of other precisions timed for one step each")
+    p.add_argument("--compare", default="fp16,fp32", help="comma list of other precisions timed for one step each")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
 
