@@ -357,6 +357,46 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         uint32_t *bj = band_j + threadIdx.x;
         float *stg = stage_v + threadIdx.x * kStageStride;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        // Fast test of 32 values against the row's threshold: a 3-input integer min over the
+        // FP32 bit patterns.  For non-negative values the integer order is the float order;
+        // a negative value compares below every non-negative threshold, so it can only raise
+        // a false alarm, which the exact walk below rejects.
+        auto imin32 = [&](const uint32_t(&w)[32]) {
+            int l1[11];
+#pragma unroll
+            for (int q = 0; q < 10; ++q) l1[q] = __vimin3_s32((int)w[3 * q], (int)w[3 * q + 1], (int)w[3 * q + 2]);
+            l1[10] = min((int)w[30], (int)w[31]);
+            const int l2a = __vimin3_s32(l1[0], l1[1], l1[2]), l2b = __vimin3_s32(l1[3], l1[4], l1[5]);
+            const int l2c = __vimin3_s32(l1[6], l1[7], l1[8]), l2d = min(l1[9], l1[10]);
+            return min(__vimin3_s32(l2a, l2b, l2c), l2d);
+        };
+        // The exact walk of one 32-column chunk through this thread's shared-memory row.
+        auto walk = [&](const uint32_t(&w)[32], int64_t jbase) {
+            const float thr = COLLECT ? cthr : sel.thr;
+            uint32_t mask = 0;
+#pragma unroll
+            for (int q = 0; q < 32; q += 4)
+                *reinterpret_cast<float4 *>(stg + q) = make_float4(__uint_as_float(w[q]), __uint_as_float(w[q + 1]),
+                                                                   __uint_as_float(w[q + 2]), __uint_as_float(w[q + 3]));
+#pragma unroll
+            for (int q = 0; q < 32; ++q) mask |= (__uint_as_float(w[q]) <= thr ? 1u : 0u) << q;
+            while (mask) {
+                const int q = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float val = stg[q];
+                const int64_t j = jbase + q;
+                if (!(val <= (COLLECT ? cthr : sel.thr))) continue;
+                if (j >= ce || (uint32_t)j == myrow) continue;
+                if (a.comp && a.comp[j] == mycomp) continue;
+                if (COLLECT) {
+                    const int64_t sl = slot0 + myrow_slot;
+                    const uint32_t p = atomicAdd(&a.coll_cnt[sl], 1u);
+                    if ((int64_t)p < a.coll_cap) a.coll_j[sl * a.coll_cap + p] = (uint32_t)j;
+                } else {
+                    sel.insert(val, (uint32_t)j, a.sc, rc, bv, bj, kRowTile);
+                }
+            }
+        };
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1;
             int ok = 1;
@@ -368,68 +408,28 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             tc_fence_after();
             const int64_t col0 = cb + (int64_t)t * kBN;
+            const uint32_t taddr = lane_base + (uint32_t)((b * 2 + half) * kBN);
 #pragma unroll 1
             for (int hh = 0; hh < kBN / 64; ++hh) {
-                uint32_t v[64];
-                uint32_t(&v0)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[0]);
-                uint32_t(&v1)[32] = *reinterpret_cast<uint32_t(*)[32]>(&v[32]);
-                const uint32_t taddr = lane_base + (uint32_t)((b * 2 + half) * kBN + hh * 64);
-                tmem_ld32(taddr, v0);
-                tmem_ld32(taddr + 32, v1);
-                tmem_wait_ld(v0);
-                reg_fence(v1);
-                const float thr = COLLECT ? cthr : sel.thr;
-                float mn[2];
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const uint32_t *w = v + c * 32;
-                    float l1[11];
-#pragma unroll
-                    for (int q = 0; q < 10; ++q)
-                        l1[q] = min3f(__uint_as_float(w[3 * q]), __uint_as_float(w[3 * q + 1]),
-                                      __uint_as_float(w[3 * q + 2]));
-                    l1[10] = fminf(__uint_as_float(w[30]), __uint_as_float(w[31]));
-                    const float l2a = min3f(l1[0], l1[1], l1[2]), l2b = min3f(l1[3], l1[4], l1[5]);
-                    const float l2c = min3f(l1[6], l1[7], l1[8]), l2d = fminf(l1[9], l1[10]);
-                    mn[c] = fminf(min3f(l2a, l2b, l2c), l2d);
+                uint32_t va[32], vb[32];
+                tmem_ld32(taddr + hh * 64, va);
+                tmem_ld32(taddr + hh * 64 + 32, vb);
+                tmem_wait_ld(va);
+                reg_fence(vb);
+                if (hh == kBN / 64 - 1) {
+                    // every load of this tile has landed: hand the TMEM buffer back early
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sh->tempty[b]);
                 }
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (!(mn[c] <= (COLLECT ? cthr : sel.thr))) continue;
-                    // rare: stage the 32 values in this thread's shared-memory row, walk the hits
-                    const uint32_t *w = v + c * 32;
-                    uint32_t mask = 0;
-#pragma unroll
-                    for (int q = 0; q < 32; q += 4) {
-                        *reinterpret_cast<float4 *>(stg + q) =
-                            make_float4(__uint_as_float(w[q]), __uint_as_float(w[q + 1]), __uint_as_float(w[q + 2]),
-                                        __uint_as_float(w[q + 3]));
-                    }
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) mask |= (__uint_as_float(w[q]) <= thr ? 1u : 0u) << q;
-                    const int64_t jbase = col0 + hh * 64 + c * 32;
-                    while (mask) {
-                        const int q = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const float val = stg[q];
-                        const int64_t j = jbase + q;
-                        if (!(val <= (COLLECT ? cthr : sel.thr))) continue;
-                        if (j >= ce || (uint32_t)j == myrow) continue;
-                        if (a.comp && a.comp[j] == mycomp) continue;
-                        if (COLLECT) {
-                            const int64_t sl = slot0 + myrow_slot;
-                            const uint32_t p = atomicAdd(&a.coll_cnt[sl], 1u);
-                            if ((int64_t)p < a.coll_cap) a.coll_j[sl * a.coll_cap + p] = (uint32_t)j;
-                        } else {
-                            sel.insert(val, (uint32_t)j, a.sc, rc, bv, bj, kRowTile);
-                        }
-                    }
+                const int ithr = __float_as_int(COLLECT ? cthr : sel.thr);
+                const int m0 = imin32(va), m1 = imin32(vb);
+                if (min(m0, m1) <= ithr) {
+                    if (m0 <= ithr) walk(va, col0 + hh * 64);
+                    if (m1 <= __float_as_int(COLLECT ? cthr : sel.thr)) walk(vb, col0 + hh * 64 + 32);
                 }
                 __syncwarp();
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sh->tempty[b]);
         }
         if (!COLLECT && valid) {
             const int64_t rec = (slot0 + myrow_slot) * a.splits + split;
