@@ -194,6 +194,33 @@ const char *nnm_status_string(nnm_status s);
 /* nnm_destroy -- free the context and its device workspace.  NULL is ignored. */
 void nnm_destroy(nnm_ctx *ctx);
 
+/* Largest N accepted by nnm_restrict_static. */
+#define NNM_STATIC_MAX_ROWS (1 << 20)
+
+/* nnm_restrict_static -- the restriction walk and the labels of nnm_cluster, applied to
+ * a merge tree the caller already holds, without allocating any device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate at call time (device memory owned by an application pool or arena that must
+ * not see foreign cudaMalloc/cudaFree, which synchronise the device and fragment the
+ * pool; services with a memory budget fixed at start-up).  Its scratch is one fixed
+ * device array of about 21 MB inside this library, held on every GPU that loads the
+ * library until the process exits.
+ *   tree_dev       nnm_edge [n_edges] device, sorted by key (as nnm_get_tree returns it);
+ *                  0 <= n_edges <= N-1.
+ *   N              rows, 2 <= N <= NNM_STATIC_MAX_ROWS (larger N: NNM_EUNSUPPORTED, no launch).
+ *   restrictions   as for nnm_cluster (may be NULL); same EINVAL / EUNSUPPORTED rules.
+ *   merges_dev, n_merges_host, labels_dev, n_clusters_host  as for nnm_cluster.
+ *   cuda_stream    cudaStream_t to enqueue on (NULL: the legacy default stream); the call
+ *                  returns after its work has completed.
+ * The first call on each device looks up the scratch array's device address, with that
+ * device current; make it before any stream capture.  All calls share the array: calls
+ * whose work overlaps on the GPU race and corrupt each other; calls ordered on one
+ * stream are safe.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
+nnm_status nnm_restrict_static(const nnm_edge *tree_dev, int64_t n_edges, int64_t N,
+                               const nnm_restrictions *restrictions, nnm_merge *merges_dev,
+                               int64_t *n_merges_host, int32_t *labels_dev, int64_t *n_clusters_host,
+                               void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

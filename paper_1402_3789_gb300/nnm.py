@@ -61,7 +61,8 @@ class nnm_stats(ctypes.Structure):
 
 # every symbol include/nnm.h declares
 EXPORTS = ("nnm_create", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats", "nnm_last_error",
-           "nnm_status_string", "nnm_destroy")
+           "nnm_status_string", "nnm_destroy", "nnm_restrict_static")
+STATIC_MAX_ROWS = 1 << 20
 
 _LIB = None
 
@@ -100,6 +101,9 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.nnm_status_string.restype = ctypes.c_char_p
     lib.nnm_destroy.argtypes = [P]
     lib.nnm_destroy.restype = None
+    lib.nnm_restrict_static.argtypes = [P, i64, i64, ctypes.POINTER(nnm_restrictions), P, ctypes.POINTER(i64), P,
+                                        ctypes.POINTER(i64), P]
+    lib.nnm_restrict_static.restype = ctypes.c_int
     _LIB = lib
     return lib
 
@@ -207,6 +211,26 @@ def nnm_destroy(ctx: Context) -> None:
     if ctx.handle:
         load_library().nnm_destroy(ctx.handle)
         ctx.handle = ctypes.c_void_p()
+
+
+def nnm_restrict_static(tree_dev: torch.Tensor, n_edges: int, N: int, restrictions=None,
+                        stream: torch.cuda.Stream | None = None) -> ClusterResult:
+    """nnm_restrict_static: restrictions + labels on a key-sorted tree (uint8 device bytes
+    of nnm_edge records), using the library's fixed scratch array (no allocation inside
+    the library; the output tensors are allocated here by the caller's allocator)."""
+    lib = load_library()
+    stream = stream or torch.cuda.current_stream(tree_dev.device)
+    merges = torch.empty(max(N - 1, 1) * MERGE_DTYPE.itemsize, dtype=torch.uint8, device=tree_dev.device)
+    labels = torch.empty(N, dtype=torch.int32, device=tree_dev.device)
+    r = _restrictions(restrictions)
+    n_m, n_c = ctypes.c_int64(), ctypes.c_int64()
+    st = lib.nnm_restrict_static(ctypes.c_void_p(tree_dev.data_ptr()), n_edges, N, ctypes.byref(r),
+                                 ctypes.c_void_p(merges.data_ptr()), ctypes.byref(n_m),
+                                 ctypes.c_void_p(labels.data_ptr()), ctypes.byref(n_c),
+                                 ctypes.c_void_p(stream.cuda_stream))
+    if st != NNM_OK:
+        raise NNMError(st, "nnm_restrict_static failed")
+    return ClusterResult(merges, n_m.value, labels, n_c.value)
 
 
 def nnm_status_string(status: int) -> str:

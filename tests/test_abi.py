@@ -27,7 +27,7 @@ def lib():
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
     assert set(names) == {"nnm_create", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats",
-                          "nnm_last_error", "nnm_status_string", "nnm_destroy"}
+                          "nnm_last_error", "nnm_status_string", "nnm_destroy", "nnm_restrict_static"}
     for n in names:
         assert hasattr(lib, n), n
     from paper_1402_3789_gb300 import nnm
