@@ -38,7 +38,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="bf16", choices=["bf16", "fp16", "fp32"])
+    p.add_argument("--precision", default="bf16", choices=["bf16", "bf16x3", "fp16", "fp32"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--n", type=int, default=None, help="override N (smaller runs)")
     p.add_argument("--no-e2e", action="store_true")
@@ -275,7 +275,8 @@ def run_ours(args, world, rank, local):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"bf16": "bf16+f64", "fp16": "f16+f64", "fp32": "f32+f64"}[args.precision],
+            "vs_baseline": None, "dtype": {"bf16": "bf16+f64", "bf16x3": "bf16x3+f64", "fp16": "f16+f64",
+                      "fp32": "f32+f64"}[args.precision],
             "data": "synthetic",
             "config": {"workload": args.workload, "N": N, "d": d, "precision": args.precision,
                        "restrictions": restr, "parallelism": "replicas" if world > 1 else "single",

@@ -54,11 +54,15 @@ typedef enum { NNM_EUCLIDEAN = 0 } nnm_metric;
  *   NNM_PREC_FP32          direct differences sum((x-y)^2) in FP32 on CUDA cores.
  *   NNM_PREC_BF16_RERANK   |x|^2 + |y|^2 - 2 x.y as a BF16 tensor-core (tcgen05)
  *                          product with FP32 accumulation, centred data.
- *   NNM_PREC_FP16_RERANK   the same with FP16 operands and one power-of-two scale. */
+ *   NNM_PREC_FP16_RERANK   the same with FP16 operands and one power-of-two scale.
+ *   NNM_PREC_BF16X3_RERANK BF16 operands with each value split as hi + lo (three
+ *                          products per feature, K = 3d + 6 padded to 16): BF16 tensor
+ *                          math with a 16-bit mantissa; d <= 30. */
 typedef enum {
     NNM_PREC_FP32 = 0,
     NNM_PREC_BF16_RERANK = 1,
-    NNM_PREC_FP16_RERANK = 2
+    NNM_PREC_FP16_RERANK = 2,
+    NNM_PREC_BF16X3_RERANK = 3
 } nnm_precision;
 
 typedef struct nnm_ctx nnm_ctx;
@@ -150,7 +154,7 @@ typedef struct {
  *   options      may be NULL.
  *   out     receives the context (NULL on failure).
  * Errors: EINVAL (sizes, null pointers), ENONFINITE (NaN/Inf in X), EUNSUPPORTED
- * (metric or precision), ENOMEM, ECUDA.  The context owns its device workspace:
+ * (metric or precision; NNM_PREC_BF16X3_RERANK with d > 30), ENOMEM, ECUDA.  The context owns its device workspace:
  * about N*(4*d_pad + 2*2*K_pad + 24*cache_k + 96) bytes. */
 nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metric,
                       nnm_precision precision, void *cuda_stream, const nnm_options *options,

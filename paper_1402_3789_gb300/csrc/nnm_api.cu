@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <string>
+#include <utility>
 
 #include "nnm_internal.cuh"
 
@@ -40,9 +41,12 @@ struct nnm_ctx {
     int dp = 0;
     int kpad = 0;
     int fp16 = 0;
+    int terms = 1;   // 3: split BF16 operands
     double scale = 1.0;
     Margin margin{};
     SelConst selc{};
+    // spatial order of the operands (see prep.cu)
+    uint32_t *pos2row = nullptr, *row2pos = nullptr, *list_pos = nullptr;
     // operands
     float *Xs = nullptr;
     uint16_t *XA = nullptr, *XB = nullptr;
@@ -58,6 +62,9 @@ struct nnm_ctx {
     uint32_t *coll_cnt = nullptr, *coll_j = nullptr;
     double *coll_D = nullptr;
     size_t coll_cap = 0;         // entries
+    uint32_t *heavy_idx = nullptr, *heavy_rows = nullptr, *heavy_rows2 = nullptr;
+    float *heavy_thr = nullptr, *heavy_thr2 = nullptr;
+    size_t heavy_cap = 0;        // rows
     // cache and rounds
     int kc = 0;
     uint32_t *cache_j = nullptr;
@@ -65,7 +72,8 @@ struct nnm_ctx {
     uint8_t *cache_n = nullptr, *cache_exh = nullptr;
     uint32_t *comp = nullptr, *parent = nullptr, *list = nullptr;
     unsigned long long *row_D = nullptr, *row_ab = nullptr, *best_D = nullptr, *best_ab = nullptr;
-    uint8_t *row_state = nullptr, *frozen = nullptr;
+    uint8_t *row_state = nullptr, *frozen = nullptr, *flag_pos = nullptr;
+    uint32_t *block_cnt = nullptr;
     nnm_edge *edges = nullptr, *edges_tmp = nullptr, *tree = nullptr;
     int64_t n_tree = 0;
     // restriction walk / labels
@@ -222,6 +230,18 @@ nnm_status ensure_ovf(nnm_ctx *c, size_t slots)
     return NNM_OK;
 }
 
+nnm_status ensure_heavy(nnm_ctx *c, size_t rows)
+{
+    if (rows <= c->heavy_cap) return NNM_OK;
+    NNM_TRY(dalloc(c, &c->heavy_idx, rows));
+    NNM_TRY(dalloc(c, &c->heavy_rows, rows));
+    NNM_TRY(dalloc(c, &c->heavy_rows2, rows));
+    NNM_TRY(dalloc(c, &c->heavy_thr, rows));
+    NNM_TRY(dalloc(c, &c->heavy_thr2, rows));
+    c->heavy_cap = rows;
+    return NNM_OK;
+}
+
 nnm_status ensure_coll(nnm_ctx *c, size_t entries)
 {
     if (entries <= c->coll_cap) return NNM_OK;
@@ -240,9 +260,11 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.XB = c->XB;
     a.kpad = c->kpad;
     a.fp16 = c->fp16;
+    a.band = c->prec == NNM_PREC_BF16_RERANK ? 64 : 32;
     a.N = c->N;
     a.col_begin = 0;
     a.col_end = c->N;
+    a.pos2row = c->pos2row;
     a.err_flag = &c->derr[0];
     a.m = c->margin;
     a.sc = c->selc;
@@ -268,6 +290,93 @@ nnm_status check_sweep_error(nnm_ctx *c)
     if (h) {
         NNM_CUDA(c, cudaMemsetAsync(&c->derr[0], 0, sizeof(int), c->stream));
         return fail(c, NNM_ETIMEOUT, "a bounded wait in the tensor-core sweep gave up");
+    }
+    return NNM_OK;
+}
+
+constexpr size_t kCollectBytes = (size_t)4 << 30;   // collect buffers (uint32 + binary64 per entry)
+
+// Collect pass over n rows (positions rows[], thresholds thr[]) with room for cap
+// columns per row; rows that collected more are gathered and run again with room for
+// their exact count.
+nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n, int64_t cap, int k,
+                   const uint32_t *comp, uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh)
+{
+    cudaStream_t s = c->stream;
+    NNM_TRY(ensure_heavy(c, (size_t)n));
+    for (int pass = 0; n > 0; ++pass) {
+        if (pass > 2) return fail(c, NNM_ECUDA, "collect pass did not converge");
+        if (cap > c->N) cap = c->N;
+        if (cap < 1) cap = 1;
+        int64_t batch = (int64_t)(kCollectBytes / 12 / (size_t)cap);
+        if (batch < 1) batch = 1;
+        if (batch > n) batch = n;
+        NNM_TRY(ensure_coll(c, (size_t)batch * cap));
+        NNM_CUDA(c, cudaMemsetAsync(&c->dcount[5], 0, sizeof(uint32_t), s));
+        NNM_CUDA(c, cudaMemsetAsync(&c->dstat[12], 0, sizeof(unsigned long long), s));
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int64_t nb = n - b0 < batch ? n - b0 : batch;
+            SweepArgs ca = base_sweep(c);
+            ca.rows = rows + b0;
+            ca.nslots = nb;
+            ca.comp = comp;
+            const int S2 = choose_splits(c, nb);
+            ca.cols_per_split = round_up((c->N + S2 - 1) / S2, 128);
+            ca.splits = (int)((c->N + ca.cols_per_split - 1) / ca.cols_per_split);
+            ca.thr = thr + b0;
+            ca.coll_cnt = c->coll_cnt;
+            ca.coll_j = c->coll_j;
+            ca.coll_cap = cap;
+            {
+                Phase ph(c, &c->stats.ms_sweep);
+                NNM_CUDA(c, cudaMemsetAsync(c->coll_cnt, 0, nb * sizeof(uint32_t), s));
+                NNM_TRY(launch_sweep(c, ca, true));
+            }
+            if (is_tensor(c)) NNM_TRY(check_sweep_error(c));
+            Phase ph(c, &c->stats.ms_rerank);
+            CollectRerankArgs ra{};
+            ra.X = c->X;
+            ra.d = c->d;
+            ra.N = c->N;
+            ra.rows = rows + b0;
+            ra.pos2row = c->pos2row;
+            ra.n = nb;
+            ra.coll_cnt = c->coll_cnt;
+            ra.coll_j = c->coll_j;
+            ra.cap = cap;
+            ra.scratch_D = c->coll_D;
+            ra.k = k;
+            ra.m = c->margin;
+            ra.res_j = res_j;
+            ra.res_D = res_D;
+            ra.res_n = res_n;
+            ra.res_exh = res_exh;
+            ra.retry_flag = &c->derr[1];
+            ra.heavy_cnt = &c->dcount[5];
+            ra.heavy_idx = c->heavy_idx;
+            ra.heavy_base = b0;
+            ra.heavy_max = &c->dstat[12];
+            ra.st_pairs = &c->dstat[2];
+            ra.st_max_cand = &c->dstat[3];
+            NNM_CUDA(c, launch_collect_rerank(ra, s));
+        }
+        uint32_t nheavy = 0;
+        unsigned long long hmax = 0;
+        NNM_CUDA(c, cudaMemcpyAsync(&nheavy, &c->dcount[5], sizeof nheavy, cudaMemcpyDeviceToHost, s));
+        NNM_CUDA(c, cudaMemcpyAsync(&hmax, &c->dstat[12], sizeof hmax, cudaMemcpyDeviceToHost, s));
+        NNM_CUDA(c, cudaStreamSynchronize(s));
+        if (nheavy == 0) break;
+        // the next pass runs only the heavy rows, with room for the largest exact count
+        NNM_CUDA(c, launch_gather_u32(c->heavy_idx, rows, nheavy, c->heavy_rows, s));
+        NNM_CUDA(c, launch_gather_f32(c->heavy_idx, thr, nheavy, c->heavy_thr, s));
+        NNM_CUDA(c, cudaStreamSynchronize(s));
+        // swap: the gathered lists become this function's inputs
+        std::swap(c->heavy_rows, c->heavy_rows2);
+        std::swap(c->heavy_thr, c->heavy_thr2);
+        rows = c->heavy_rows2;
+        thr = c->heavy_thr2;
+        n = nheavy;
+        cap = (int64_t)hmax;
     }
     return NNM_OK;
 }
@@ -318,6 +427,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
         fa.d = c->d;
         fa.N = c->N;
         fa.rows = rows;
+        fa.pos2row = c->pos2row;
         fa.nslots = nslots;
         fa.splits = splits;
         fa.in_v = c->cand_v;
@@ -341,58 +451,12 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     }
     if (novf == 0) return NNM_OK;
 
-    // collect pass: every eligible column with value <= the row's threshold
+    // Collect pass: every eligible column with value <= the row's threshold.  The first
+    // pass gives each row room for cap columns and counts exactly; rows that had more are
+    // run again with room for all of them.  Batches keep the buffers within kCollectBytes.
     c->stats.rows_overflowed += novf;
-    int64_t cap = is_tensor(c) ? 1024 : 256;
-    for (int attempt = 0;; ++attempt) {
-        if (cap > c->N) cap = c->N;
-        NNM_TRY(ensure_coll(c, (size_t)novf * cap));
-        SweepArgs ca = base_sweep(c);
-        ca.rows = c->ovf_row;
-        ca.nslots = novf;
-        ca.comp = comp;
-        const int S2 = choose_splits(c, novf);
-        ca.cols_per_split = round_up((c->N + S2 - 1) / S2, 128);
-        ca.splits = (int)((c->N + ca.cols_per_split - 1) / ca.cols_per_split);
-        ca.thr = c->ovf_thr;
-        ca.coll_cnt = c->coll_cnt;
-        ca.coll_j = c->coll_j;
-        ca.coll_cap = cap;
-        {
-            Phase ph(c, &c->stats.ms_sweep);
-            NNM_CUDA(c, cudaMemsetAsync(c->coll_cnt, 0, novf * sizeof(uint32_t), c->stream));
-            NNM_TRY(launch_sweep(c, ca, true));
-        }
-        if (is_tensor(c)) NNM_TRY(check_sweep_error(c));
-        int retry = 0;
-        {
-            Phase ph(c, &c->stats.ms_rerank);
-            NNM_CUDA(c, cudaMemsetAsync(&c->derr[1], 0, sizeof(int), c->stream));
-            CollectRerankArgs ra{};
-            ra.X = c->X;
-            ra.d = c->d;
-            ra.N = c->N;
-            ra.rows = c->ovf_row;
-            ra.n = novf;
-            ra.coll_cnt = c->coll_cnt;
-            ra.coll_j = c->coll_j;
-            ra.cap = cap;
-            ra.scratch_D = c->coll_D;
-            ra.k = k;
-            ra.res_j = res_j;
-            ra.res_D = res_D;
-            ra.res_n = res_n;
-            ra.res_exh = res_exh;
-            ra.retry_flag = &c->derr[1];
-            ra.st_pairs = &c->dstat[2];
-            ra.st_max_cand = &c->dstat[3];
-            NNM_CUDA(c, launch_collect_rerank(ra, c->stream));
-            NNM_CUDA(c, cudaMemcpyAsync(&retry, &c->derr[1], sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        }
-        if (!retry) break;
-        if (cap >= c->N || attempt > 8) return fail(c, NNM_ECUDA, "collect pass did not converge");
-        cap *= 4;
-    }
+    NNM_TRY(collect(c, c->ovf_row, c->ovf_thr, novf, is_tensor(c) ? 1024 : 256, k, comp, res_j, res_D, res_n,
+                    res_exh));
     return NNM_OK;
 }
 
@@ -444,10 +508,28 @@ nnm_status prepare(nnm_ctx *c)
     NNM_CUDA(c, cudaStreamSynchronize(s));
     if (bad) return fail(c, NNM_ENONFINITE, "X holds NaN or infinite values");
 
+    // spatial order: landmark groups, sorted by (group, distance to the landmark, row)
+    {
+        NNM_TRY(dalloc(c, &c->pos2row, (size_t)c->N));
+        NNM_TRY(dalloc(c, &c->row2pos, (size_t)c->N));
+        NNM_TRY(dalloc(c, &c->list_pos, (size_t)c->N));
+        nnm_edge *keys = nullptr, *tmp = nullptr, *sorted = nullptr;
+        NNM_TRY(dalloc(c, &keys, (size_t)c->N));
+        NNM_TRY(dalloc(c, &tmp, (size_t)c->N));
+        int64_t L = c->N / 256;
+        if (L > 1024) L = 1024;
+        if (L < 1) L = 1;
+        NNM_CUDA(c, launch_landmark_keys(c->X, c->N, c->d, L, keys, s));
+        NNM_CUDA(c, launch_sort_edges(keys, tmp, c->N, s, &sorted));
+        NNM_CUDA(c, launch_order_from_keys(sorted, c->N, c->pos2row, c->row2pos, s));
+        NNM_CUDA(c, cudaStreamSynchronize(s));
+        cudaFree(keys);
+        cudaFree(tmp);
+    }
     if (!is_tensor(c)) {
         c->dp = (c->d + 3) & ~3;
         NNM_TRY(dalloc(c, &c->Xs, (size_t)c->Npad * c->dp));
-        NNM_CUDA(c, launch_pad_fp32(c->X, c->N, c->d, c->dp, c->Npad, c->Xs, s));
+        NNM_CUDA(c, launch_pad_fp32(c->X, c->N, c->d, c->dp, c->Npad, c->pos2row, c->Xs, s));
         const double u = 0x1p-24;
         c->margin.tensor = 0;
         c->margin.gamma = (c->d + 2) * u / (1.0 - (c->d + 2) * u);
@@ -455,7 +537,8 @@ nnm_status prepare(nnm_ctx *c)
         c->margin.inv_scale2 = 1.0;
     } else {
         c->fp16 = c->prec == NNM_PREC_FP16_RERANK;
-        c->kpad = (int)round_up(c->d + 6, 16);
+        c->terms = c->prec == NNM_PREC_BF16X3_RERANK ? 3 : 1;
+        c->kpad = (int)round_up(c->terms * c->d + 6, 16);
         const int mb = mean_blocks(c->N);
         double *partial = nullptr, *mu = nullptr;
         NNM_TRY(dalloc(c, &partial, (size_t)mb * c->d));
@@ -476,8 +559,8 @@ nnm_status prepare(nnm_ctx *c)
         NNM_TRY(dalloc(c, &c->r, (size_t)c->Npad));
         NNM_TRY(dalloc(c, &c->P, (size_t)c->Npad));
         NNM_TRY(dalloc(c, &c->E, (size_t)c->Npad));
-        NNM_CUDA(c, launch_tc_operands(c->X, c->N, c->d, mu, c->scale, c->fp16, c->kpad, c->Npad, c->XA, c->XB,
-                                       c->r, c->P, c->E, &c->dstat[9], s));
+        NNM_CUDA(c, launch_tc_operands(c->X, c->N, c->d, mu, c->scale, c->fp16, c->terms, c->kpad, c->Npad, c->row2pos, c->XA,
+                                       c->XB, c->r, c->P, c->E, &c->dstat[9], s));
         unsigned long long mx[3];
         NNM_CUDA(c, cudaMemcpyAsync(mx, &c->dstat[9], sizeof mx, cudaMemcpyDeviceToHost, s));
         NNM_CUDA(c, cudaStreamSynchronize(s));
@@ -497,6 +580,11 @@ nnm_status prepare(nnm_ctx *c)
         c->margin.E = c->E;
         c->stats.k_pad = c->kpad;
         c->stats.scale = c->scale;
+    }
+    {
+        const double u = 0x1p-24;
+        c->margin.gamma32 = (c->d + 2) * u / (1.0 - (c->d + 2) * u);
+        c->margin.alpha32 = (c->d + 2) * 0x1p-149;
     }
     c->selc = make_selconst(c->margin);
     return NNM_OK;
@@ -518,6 +606,8 @@ nnm_status ensure_rounds(nnm_ctx *c)
     NNM_TRY(dalloc(c, &c->best_ab, (size_t)N));
     NNM_TRY(dalloc(c, &c->row_state, (size_t)N));
     NNM_TRY(dalloc(c, &c->frozen, (size_t)N));
+    NNM_TRY(dalloc(c, &c->flag_pos, (size_t)N));
+    NNM_TRY(dalloc(c, &c->block_cnt, (size_t)((N + 1023) / 1024)));
     NNM_TRY(dalloc(c, &c->edges, (size_t)N));
     NNM_TRY(dalloc(c, &c->edges_tmp, (size_t)N));
     NNM_TRY(dalloc(c, &c->uf_parent, (size_t)N));
@@ -561,6 +651,11 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     st.best_D = c->best_D;
     st.best_ab = c->best_ab;
     st.list = c->list;
+    st.list_pos = c->list_pos;
+    st.flag_pos = c->flag_pos;
+    st.block_cnt = c->block_cnt;
+    st.row2pos = c->row2pos;
+    st.pos2row = c->pos2row;
     st.counters = &c->dcount[1];
     st.edges = c->edges;
     st.n_edges = &c->dcount[4];
@@ -580,13 +675,12 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
             Phase ph(c, &c->stats.ms_rounds);
             NNM_CUDA(c, launch_resolve(st, nullptr, c->N, s));
             NNM_CUDA(c, launch_component_min(st, s));
-            NNM_CUDA(c, cudaMemsetAsync(&c->dcount[1], 0, sizeof(uint32_t), s));
             NNM_CUDA(c, launch_flag_rescans(st, s));
         }
         NNM_TRY(read_dev(c, &nres, &c->dcount[1]));
         if (nres > 0) {
             c->stats.rows_rescanned += nres;
-            NNM_TRY(run_knn(c, c->list, nres, c->kc, c->comp, c->cache_j, c->cache_D, c->cache_n, c->cache_exh,
+            NNM_TRY(run_knn(c, c->list_pos, nres, c->kc, c->comp, c->cache_j, c->cache_D, c->cache_n, c->cache_exh,
                             false));
             Phase ph(c, &c->stats.ms_rounds);
             NNM_CUDA(c, launch_resolve(st, c->list, nres, s));
@@ -649,8 +743,10 @@ nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metri
     *out = nullptr;
     if (!X_dev || N < 1 || N >= (int64_t(1) << 31) || d < 1 || d > 32) return NNM_EINVAL;
     if (metric != NNM_EUCLIDEAN) return NNM_EUNSUPPORTED;
-    if (precision != NNM_PREC_FP32 && precision != NNM_PREC_BF16_RERANK && precision != NNM_PREC_FP16_RERANK)
+    if (precision != NNM_PREC_FP32 && precision != NNM_PREC_BF16_RERANK && precision != NNM_PREC_FP16_RERANK &&
+        precision != NNM_PREC_BF16X3_RERANK)
         return NNM_EUNSUPPORTED;
+    if (precision == NNM_PREC_BF16X3_RERANK && d > 30) return NNM_EUNSUPPORTED;
     if (options && (options->cache_k < 0 || options->cache_k > 16 || options->col_split < 0)) return NNM_EINVAL;
     nnm_ctx *c = new nnm_ctx();
     c->X = X_dev;
@@ -782,6 +878,9 @@ void nnm_destroy(nnm_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    dfree(c->pos2row);
+    dfree(c->row2pos);
+    dfree(c->list_pos);
     dfree(c->Xs);
     dfree(c->XA);
     dfree(c->XB);
@@ -796,6 +895,11 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->coll_cnt);
     dfree(c->coll_j);
     dfree(c->coll_D);
+    dfree(c->heavy_idx);
+    dfree(c->heavy_rows);
+    dfree(c->heavy_rows2);
+    dfree(c->heavy_thr);
+    dfree(c->heavy_thr2);
     dfree(c->cache_j);
     dfree(c->cache_D);
     dfree(c->cache_n);
@@ -809,6 +913,8 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->best_ab);
     dfree(c->row_state);
     dfree(c->frozen);
+    dfree(c->flag_pos);
+    dfree(c->block_cnt);
     dfree(c->edges);
     dfree(c->edges_tmp);
     dfree(c->uf_parent);

@@ -16,7 +16,7 @@ void count_launches(int n);
 int64_t launches_so_far();
 
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
-constexpr int kListC = 48;        // record slots per (row, column range): 16 top + 32 band
+constexpr int kListC = 80;        // record slots per (row, column range): 16 top + up to 64 band
 constexpr int kMaxK = 16;         // largest k of nnm_nearest / cache width
 constexpr int kRowTile = 256;     // rows per sweep CTA (both candidate paths)
 constexpr int kMaxSplits = 32;    // column ranges per row tile
@@ -33,6 +33,8 @@ struct Margin {
     const float *r;     // tensor: per-row rounding radius
     const float *P;     // tensor: per-row |x_hat|
     const float *E;     // tensor: per-row norm-split error
+    double gamma32;     // FP32 direct refinement: relative bound gamma_{d+2}, u = 2^-24
+    double alpha32;     //   and its underflow slack
 };
 
 // Per-launch constants of the sweeps' pruning threshold (an FP32 upper bound, rounded
@@ -57,12 +59,14 @@ struct SweepArgs {
     const uint16_t *XB;       // tensor path: column operand, same layout
     int kpad;
     int fp16;                 // tensor path: 1 FP16 operands, 0 BF16
+    int band;                 // tensor path: band slots per row (32 or 64)
     int64_t N;
-    // rows
-    const uint32_t *rows;     // nullptr: slot q is row q
+    // rows and columns are positions in the spatial order of the operands
+    const uint32_t *rows;     // slot -> row position (nullptr: slot q is position q)
     int64_t nslots;
+    const uint32_t *pos2row;  // position -> original row index
     // eligibility
-    const uint32_t *comp;     // nullptr: every column j != i is eligible; else comp[j] != comp[i]
+    const uint32_t *comp;     // nullptr: every column j != i is eligible; else comp[row(j)] != comp[row(i)]
     // columns
     int64_t col_begin, col_end, cols_per_split;
     int splits;
@@ -87,7 +91,7 @@ struct SweepArgs {
 cudaError_t launch_sweep_fp32(const SweepArgs &a, int d, bool collect, cudaStream_t s);
 // Launch the tcgen05 sweep.
 cudaError_t launch_sweep_tc(const SweepArgs &a, bool collect, cudaStream_t s);
-size_t sweep_tc_smem_bytes(int kpad);
+size_t sweep_tc_smem_bytes(int kpad, int band);
 
 // ---------------------------------------------------------------------------------
 // Exact re-rank (K3)
@@ -96,7 +100,8 @@ struct FinalizeArgs {
     const float *X;            // user's rows [N][d]
     int d;
     int64_t N;
-    const uint32_t *rows;      // slot -> row (nullptr: identity)
+    const uint32_t *rows;      // slot -> row position (nullptr: identity)
+    const uint32_t *pos2row;   // position -> original row index
     int64_t nslots;
     int splits;
     const float *in_v;         // [nslots][splits][kListC]
@@ -111,7 +116,7 @@ struct FinalizeArgs {
     uint8_t *res_exh;          // 1: the results hold every eligible column (nullable)
     // incomplete rows -> collect pass
     uint32_t *ovf_cnt;         // single counter
-    uint32_t *ovf_row;         // [nslots] row index of each incomplete slot
+    uint32_t *ovf_row;         // [nslots] row position of each incomplete slot
     float *ovf_thr;            // [nslots] its threshold (rounded up)
     // statistics
     unsigned long long *st_max_abs;   // double bits
@@ -126,18 +131,24 @@ struct CollectRerankArgs {
     const float *X;
     int d;
     int64_t N;
-    const uint32_t *rows;      // collect slot p -> row index
+    const uint32_t *rows;      // collect slot p -> row position
+    const uint32_t *pos2row;   // position -> original row index
     int64_t n;                 // collect slots
     const uint32_t *coll_cnt;  // [n]
     const uint32_t *coll_j;    // [n][cap]
     int64_t cap;
     double *scratch_D;         // [n][cap]
     int k;
+    Margin m;                  // FP32 refinement bounds
     uint32_t *res_j;
     double *res_D;
     uint8_t *res_n;
     uint8_t *res_exh;
     int *retry_flag;           // set when a slot collected more than cap
+    uint32_t *heavy_cnt;       // slots that collected more than cap: count ...
+    uint32_t *heavy_idx;       // ... and their collect-slot indices (+ heavy_base)
+    int64_t heavy_base;
+    unsigned long long *heavy_max;   // largest such count
     unsigned long long *st_pairs;
     unsigned long long *st_max_cand;
 };
@@ -148,16 +159,27 @@ cudaError_t launch_collect_rerank(const CollectRerankArgs &a, cudaStream_t s);
 // Preparation
 // ---------------------------------------------------------------------------------
 cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream_t s);
-cudaError_t launch_pad_fp32(const float *X, int64_t N, int d, int dp, int64_t Npad, float *Xs,
-                            cudaStream_t s);
+// Spatial order: sort keys (landmark group, distance to it, row) for every row.
+cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, nnm_edge *keys, cudaStream_t s);
+// pos2row[p] = keys[p].a, row2pos[pos2row[p]] = p
+cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,
+                                   cudaStream_t s);
+// out[q] = map[in[q]]
+cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *map, int64_t n, uint32_t *out, cudaStream_t s);
+cudaError_t launch_gather_f32(const uint32_t *in, const float *map, int64_t n, float *out, cudaStream_t s);
+// padded FP32 copy in position order
+cudaError_t launch_pad_fp32(const float *X, int64_t N, int d, int dp, int64_t Npad, const uint32_t *pos2row,
+                            float *Xs, cudaStream_t s);
 // column means in binary64 (deterministic order); partial: [blocks][d]
 cudaError_t launch_mean(const float *X, int64_t N, int d, double *partial, int blocks, double *mu,
                         cudaStream_t s);
 int mean_blocks(int64_t N);
 cudaError_t launch_max_sqnorm(const float *X, int64_t N, int d, const double *mu,
                               unsigned long long *out_bits, cudaStream_t s);
+// operands written at each row's position; r, P, E stay indexed by original row
 cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale,
-                               int fp16, int kpad, int64_t Npad, uint16_t *XA, uint16_t *XB,
+                               int fp16, int terms, int kpad, int64_t Npad, const uint32_t *row2pos, uint16_t *XA,
+                               uint16_t *XB,
                                float *r, float *P, float *E, unsigned long long *max_bits /*[3]*/,
                                cudaStream_t s);
 
@@ -178,7 +200,11 @@ struct RoundState {
     uint8_t *row_state;            // 0 none, 1 resolved, 2 unresolved (row_D/row_ab: bound)
     unsigned long long *best_D;    // [N] per component
     unsigned long long *best_ab;
-    uint32_t *list;                // [N] rescan rows
+    uint32_t *list;                // [N] rescan rows (original indices, position order)
+    uint32_t *list_pos;            // [N] their positions, increasing
+    uint8_t *flag_pos;             // [N] rescan flag per position
+    uint32_t *block_cnt;           // [ceil(N / 1024)] compaction scratch
+    const uint32_t *row2pos, *pos2row;
     uint32_t *counters;            // [0] rescans, [1] edges this round, [2] jump changes
     nnm_edge *edges;               // [N-1]
     uint32_t *n_edges;             // device count

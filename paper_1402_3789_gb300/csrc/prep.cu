@@ -31,30 +31,137 @@ cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream
     return cudaGetLastError();
 }
 
-// Padded FP32 copy: rows [N, Npad) get a large value in every feature so that their
-// candidate values are large; they are excluded by index anyway.
+// ---------------------------------------------------------------------------------
+// Spatial order of the rows.  The sweeps read operands in an order where rows that are
+// close in space are close in memory, so that a row tile meets its near neighbours in
+// its first column tiles and far tiles can be bounded as a whole.  Rows are grouped by
+// their nearest landmark (L rows taken at regular strides), and within a group ordered
+// by their distance to the landmark, then by index: far outliers of a group end up in
+// its last tile.  The order only affects speed: every decision uses original indices
+// and the exact binary64 distance.
+// ---------------------------------------------------------------------------------
+constexpr int kLandChunk = 128;
+
+__global__ void __launch_bounds__(256) k_landmark_keys(const float *__restrict__ X, int64_t N, int d, int64_t L,
+                                                       nnm_edge *__restrict__ keys)
+{
+    __shared__ float lm[kLandChunk * 32];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float x[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] = (i < N && k < d) ? X[i * d + k] : 0.0f;
+    float best = INFINITY;
+    int64_t arg = 0;
+    for (int64_t m0 = 0; m0 < L; m0 += kLandChunk) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < kLandChunk * 32; q += blockDim.x) {
+            const int64_t m = m0 + q / 32;
+            const int k = q % 32;
+            lm[q] = (m < L && k < d) ? X[(m * N / L) * d + k] : 0.0f;
+        }
+        __syncthreads();
+        const int64_t cnt = L - m0 < kLandChunk ? L - m0 : kLandChunk;
+        for (int m = 0; m < cnt; ++m) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                const float e = x[k] - lm[m * 32 + k];
+                acc = fmaf(e, e, acc);
+            }
+            if (acc < best) {
+                best = acc;
+                arg = m0 + m;
+            }
+        }
+    }
+    if (i < N) {
+        nnm_edge e;
+        e.a = (uint32_t)i;
+        e.b = 0u;
+        e.D = (double)arg * 4294967296.0 + (double)__float_as_uint(best);   // exact: < 2^53
+        keys[i] = e;
+    }
+}
+
+cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, nnm_edge *keys, cudaStream_t s)
+{
+    k_landmark_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, N, d, L, keys);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_order_from_keys(const nnm_edge *__restrict__ keys, int64_t N, uint32_t *pos2row,
+                                  uint32_t *row2pos)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const uint32_t i = keys[p].a;
+    pos2row[p] = i;
+    row2pos[i] = (uint32_t)p;
+}
+
+cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,
+                                   cudaStream_t s)
+{
+    k_order_from_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(keys, N, pos2row, row2pos);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_u32(const uint32_t *__restrict__ in, const uint32_t *__restrict__ map, int64_t n,
+                             uint32_t *__restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = map[in[q]];
+}
+
+cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *map, int64_t n, uint32_t *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_gather_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, map, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_f32(const uint32_t *__restrict__ in, const float *__restrict__ map, int64_t n,
+                             float *__restrict__ out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = map[in[q]];
+}
+
+cudaError_t launch_gather_f32(const uint32_t *in, const float *map, int64_t n, float *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_gather_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, map, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// Padded FP32 copy in position order: positions [N, Npad) get a large value in every
+// feature so that their candidate values are large; they are excluded by index anyway.
 __global__ void k_pad_fp32(const float *__restrict__ X, int64_t N, int d, int dp, int64_t Npad,
-                           float *__restrict__ Xs)
+                           const uint32_t *__restrict__ pos2row, float *__restrict__ Xs)
 {
     int64_t total = Npad * dp;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = q / dp;
-        int k = (int)(q - i * dp);
+        int64_t p = q / dp;
+        int k = (int)(q - p * dp);
         float v = 0.0f;
-        if (i >= N) v = k < d ? 1.0e18f : 0.0f;
-        else if (k < d) v = X[i * d + k];
+        if (p >= N) v = k < d ? 1.0e18f : 0.0f;
+        else if (k < d) v = X[(int64_t)pos2row[p] * d + k];
         Xs[q] = v;
     }
 }
 
-cudaError_t launch_pad_fp32(const float *X, int64_t N, int d, int dp, int64_t Npad, float *Xs,
-                            cudaStream_t s)
+cudaError_t launch_pad_fp32(const float *X, int64_t N, int d, int dp, int64_t Npad, const uint32_t *pos2row,
+                            float *Xs, cudaStream_t s)
 {
     int64_t total = Npad * dp;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_pad_fp32<<<blocks, 256, 0, s>>>(X, N, d, dp, Npad, Xs);
+    k_pad_fp32<<<blocks, 256, 0, s>>>(X, N, d, dp, Npad, pos2row, Xs);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -163,41 +270,64 @@ __device__ __forceinline__ int64_t il_offset(int64_t i, int k, int kpad)
 }
 
 // Tensor-core operands.  With y = (x - mu) * scale (scale a power of two) and x_hat
-// its rounding, the accumulator of the row operand A_i = [x_hat_i, 1, 1, 1, a_i]
-// against the column operand B_j = [-2 x_hat_j, a_j, 1, 1, 1] is
-//     |x_hat_i|^2 + |x_hat_j|^2 - 2 x_hat_i . x_hat_j  =  |x_hat_i - x_hat_j|^2
+// its 16-bit approximation, the accumulator of the row operand A_i against the column
+// operand B_j is |x_hat_i - x_hat_j|^2 (+ a bounded term for the split form):
+//   one term  : x_hat = round16(y);  A = [x_hat, 1,1,1, a],  B = [-2 x_hat, a, 1,1,1]
+//   split (3) : x_hat = hi + lo, hi = bf16(y), lo = bf16(y - hi);
+//               A = [hi, hi, lo, 1,1,1, a],  B = [-2 hi, -2 lo, -2 hi, a, 1,1,1]
+//               so A.B = |x_hat_i|^2 + |x_hat_j|^2 - 2 x_hat_i.x_hat_j + 2 lo_i.lo_j
 // where a = (a1, a2, a3) splits the binary64 norm |x_hat|^2 into three 16-bit values.
-// Per row: r = |x_hat - y| (rounding radius, rounded up), P = |x_hat|, E = the split's
-// residual.  These bound the candidate error in the re-rank's completeness test.
+// Per row: r = |x_hat - y| (rounding radius, rounded up); P bounds the terms' size
+// (|x_hat| for one term, |hi| + |lo| for the split form); E = the norm split's residual
+// plus, for the split form, |lo|^2 (2 lo_i.lo_j <= |lo_i|^2 + |lo_j|^2).  These bound
+// the candidate error in the re-rank's completeness test.
 __global__ void k_tc_operands(const float *__restrict__ X, int64_t N, int d, const double *__restrict__ mu,
-                              double scale, int fp16, int kpad, int64_t Npad, uint16_t *__restrict__ XA,
+                              double scale, int fp16, int terms, int kpad, int64_t Npad,
+                              const uint32_t *__restrict__ row2pos, uint16_t *__restrict__ XA,
                               uint16_t *__restrict__ XB, float *__restrict__ r_out, float *__restrict__ P_out,
                               float *__restrict__ E_out, unsigned long long *max_bits)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= Npad) return;
     const uint16_t one = fp16 ? (uint16_t)0x3C00 : (uint16_t)0x3F80;
+    const int D = terms * d;   // product columns
     if (i >= N) {
         // padding column: a huge accumulator; padding row: zeros (never read back)
         const uint16_t big = fp16 ? (uint16_t)0x7800 /* 32768 */ : (uint16_t)0x7180 /* 2^100 */;
         for (int k = 0; k < kpad; ++k) {
             XA[il_offset(i, k, kpad)] = 0;
-            XB[il_offset(i, k, kpad)] = (k >= d && k < d + 3) ? big : (uint16_t)0;
+            XB[il_offset(i, k, kpad)] = (k >= D && k < D + 3) ? big : (uint16_t)0;
         }
         return;
     }
-    double rr = 0.0, n = 0.0, ynorm2 = 0.0;
+    const int64_t pos = row2pos[i];   // operands are stored in position order
+    double rr = 0.0, n = 0.0, ynorm2 = 0.0, hn = 0.0, ln = 0.0;
     for (int k = 0; k < d; ++k) {
-        double y = ((double)X[i * d + k] - mu[k]) * scale;
-        double h;
-        uint16_t bits = round16(y, fp16, &h);
-        rr += (h - y) * (h - y);
-        n += h * h;
+        const double y = ((double)X[i * d + k] - mu[k]) * scale;
+        double h, l = 0.0, t;
+        const uint16_t hb = round16(y, fp16, &h);
+        uint16_t lb = 0;
+        if (terms == 3) lb = round16(y - h, fp16, &l);
+        const double xh = h + l;   // exact: both are 16-bit values of nearby binades
+        rr += (xh - y) * (xh - y);
+        n += xh * xh;
         ynorm2 += y * y;
-        XA[il_offset(i, k, kpad)] = bits;
-        // -2 * h is exact in either format (sign flip, exponent + 1)
-        double h2;
-        XB[il_offset(i, k, kpad)] = round16(-2.0 * h, fp16, &h2);
+        hn += h * h;
+        ln += l * l;
+        // -2 * v is exact in either format (sign flip, exponent + 1)
+        const uint16_t hb2 = round16(-2.0 * h, fp16, &t);
+        if (terms == 1) {
+            XA[il_offset(pos, k, kpad)] = hb;
+            XB[il_offset(pos, k, kpad)] = hb2;
+        } else {
+            const uint16_t lb2 = round16(-2.0 * l, fp16, &t);
+            XA[il_offset(pos, k, kpad)] = hb;
+            XA[il_offset(pos, d + k, kpad)] = hb;
+            XA[il_offset(pos, 2 * d + k, kpad)] = lb;
+            XB[il_offset(pos, k, kpad)] = hb2;
+            XB[il_offset(pos, d + k, kpad)] = lb2;
+            XB[il_offset(pos, 2 * d + k, kpad)] = hb2;
+        }
     }
     double a1, a2, a3;
     uint16_t b1 = round16(n, fp16, &a1);
@@ -205,23 +335,23 @@ __global__ void k_tc_operands(const float *__restrict__ X, int64_t N, int d, con
     uint16_t b2 = round16(rem, fp16, &a2);
     double rem2 = rem - a2;
     uint16_t b3 = round16(rem2, fp16, &a3);
-    double E = fabs(rem2 - a3);
-    for (int k = d; k < kpad; ++k) {
+    double E = fabs(rem2 - a3) + ln;
+    for (int k = D; k < kpad; ++k) {
         uint16_t va = 0, vb = 0;
-        if (k < d + 3) {
+        if (k < D + 3) {
             va = one;
-            vb = k == d ? b1 : (k == d + 1 ? b2 : b3);
-        } else if (k < d + 6) {
-            va = k == d + 3 ? b1 : (k == d + 4 ? b2 : b3);
+            vb = k == D ? b1 : (k == D + 1 ? b2 : b3);
+        } else if (k < D + 6) {
+            va = k == D + 3 ? b1 : (k == D + 4 ? b2 : b3);
             vb = one;
         }
-        XA[il_offset(i, k, kpad)] = va;
-        XB[il_offset(i, k, kpad)] = vb;
+        XA[il_offset(pos, k, kpad)] = va;
+        XB[il_offset(pos, k, kpad)] = vb;
     }
     // rounding radius: |x_hat - y| plus the binary64 error of (x - mu) * scale, both
     // enlarged by a relative 1e-12 for the roundings of these bound computations
     double r = (sqrt(rr) + sqrt(ynorm2) * 0x1p-52) * (1.0 + 1e-12) + 1e-300;
-    double P = sqrt(n) * (1.0 + 1e-12);
+    double P = (terms == 1 ? sqrt(n) : sqrt(hn) + sqrt(ln)) * (1.0 + 1e-12);
     E = E * (1.0 + 1e-12);
     float rf = __double2float_ru(r), Pf = __double2float_ru(P), Ef = __double2float_ru(E);
     r_out[i] = rf;
@@ -232,12 +362,13 @@ __global__ void k_tc_operands(const float *__restrict__ X, int64_t N, int d, con
     atomic_max_nonneg(&max_bits[2], (double)Ef);
 }
 
-cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale, int fp16,
-                               int kpad, int64_t Npad, uint16_t *XA, uint16_t *XB, float *r, float *P,
-                               float *E, unsigned long long *max_bits, cudaStream_t s)
+cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale, int fp16, int terms,
+                               int kpad, int64_t Npad, const uint32_t *row2pos, uint16_t *XA, uint16_t *XB, float *r,
+                               float *P, float *E, unsigned long long *max_bits, cudaStream_t s)
 {
     int blocks = (int)((Npad + 255) / 256);
-    k_tc_operands<<<blocks, 256, 0, s>>>(X, N, d, mu, scale, fp16, kpad, Npad, XA, XB, r, P, E, max_bits);
+    k_tc_operands<<<blocks, 256, 0, s>>>(X, N, d, mu, scale, fp16, terms, kpad, Npad, row2pos, XA, XB, r, P, E,
+                                         max_bits);
     count_launches(1);
     return cudaGetLastError();
 }

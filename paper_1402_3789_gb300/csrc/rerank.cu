@@ -102,6 +102,67 @@ __device__ void select_topk(double *wD, uint32_t *wj, int n, int k, uint32_t i, 
     *n_out = cnt;
 }
 
+// FP32 direct squared distance, one FMA per feature in order (|s - exact| <= gamma32*s + alpha32).
+__device__ __forceinline__ float fp32_D(const float *__restrict__ xi, const float *__restrict__ xj, int d)
+{
+    float s = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        const float e = xi[k] - xj[k];
+        s = fmaf(e, e, s);
+    }
+    return s;
+}
+
+// Exact distances of the candidates in wD (entries < inf) of one row, cheapest first:
+// with refine, every candidate first gets its FP32 direct value s; from the k-th
+// smallest s the FP32 bound T32 (as for the FP32 sweep) keeps only the candidates that
+// can still be among the exact k nearest, and only those get the binary64 distance.
+// On return wD[e] = D (binary64) or +inf.  Returns the number of binary64 evaluations.
+__device__ int exact_distances(const float *xi, const float *X, int d, double *wD, const uint32_t *wj, int n, int k,
+                               const Margin &m, bool refine)
+{
+    const int lane = threadIdx.x & 31;
+    double T32 = INFINITY;
+    if (refine) {
+        for (int e = lane; e < n; e += 32)
+            if (wD[e] < INFINITY) wD[e] = (double)fp32_D(xi, X + (int64_t)wj[e] * d, d);
+        __syncwarp();
+        // k-th smallest s: extracted entries are marked by w -> -1 - w and restored after
+        int taken = 0;
+        double vk = INFINITY;
+        for (int mth = 0; mth < k; ++mth) {
+            Best b = {INFINITY, kInvalid, -1};
+            for (int e = lane; e < n; e += 32)
+                if (wD[e] >= 0.0 && wD[e] < INFINITY && less_dj(wD[e], (uint32_t)e, b.D, b.j)) b = {wD[e], (uint32_t)e, e};
+            b = warp_min(b);
+            if (b.e < 0) break;
+            vk = b.D;
+            ++taken;
+            if (lane == 0) wD[b.e] = -1.0 - wD[b.e];
+            __syncwarp();
+        }
+        for (int e = lane; e < n; e += 32)
+            if (wD[e] < 0.0) wD[e] = -1.0 - wD[e];
+        __syncwarp();
+        if (taken == k) {
+            const double grow = 1.0 + 1e-12;
+            const double us = (vk + m.alpha32) / (1.0 - m.gamma32) * grow;
+            T32 = (us * (1.0 + m.gamma32) + m.alpha32) * grow;
+        }
+    }
+    int nd = 0;
+    for (int e = lane; e < n; e += 32) {
+        double D = INFINITY;
+        if (wD[e] < INFINITY && wD[e] <= T32) {
+            D = canon_D(xi, X + (int64_t)wj[e] * d, d);
+            ++nd;
+        }
+        wD[e] = D;
+    }
+    __syncwarp();
+    return __reduce_add_sync(0xffffffffu, nd);
+}
+
 __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs a)
 {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -116,14 +177,15 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
                    (size_t)warp * n_ent;
     const int64_t q = (int64_t)blockIdx.x * kFinWarps + warp;
     if (q >= a.nslots) return;
-    const uint32_t i = a.rows ? a.rows[q] : (uint32_t)q;
+    const uint32_t ipos = a.rows ? a.rows[q] : (uint32_t)q;
+    const uint32_t i = a.pos2row[ipos];
     const float *vin = a.in_v + q * n_ent;
     const uint32_t *jin = a.in_j + q * n_ent;
     for (int e = lane; e < n_ent; e += 32) {
-        const uint32_t j = jin[e];
+        const uint32_t j = jin[e];   // a position; from here on original row indices
         const float v = vin[e];
         wv[e] = v;
-        wj[e] = j;
+        wj[e] = j != kInvalid ? a.pos2row[j] : kInvalid;
         wD[e] = j != kInvalid ? (double)v : INFINITY;
     }
     const bool ovf = lane < a.splits && a.in_ovf[q * a.splits + lane];
@@ -146,30 +208,25 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     if (__any_sync(0xffffffffu, ovf)) {
         if (lane == 0) {
             const uint32_t p = atomicAdd(a.ovf_cnt, 1u);
-            a.ovf_row[p] = i;
+            a.ovf_row[p] = ipos;
             a.ovf_thr[p] = __double2float_ru(T);
         }
         return;
     }
     const float *xi = a.X + (int64_t)i * a.d;
-    int ncand = 0;
+    for (int e = lane; e < n_ent; e += 32) wD[e] = (wj[e] != kInvalid && (double)wv[e] <= T) ? 0.0 : INFINITY;
+    __syncwarp();
+    const int nc = exact_distances(xi, a.X, a.d, wD, wj, n_ent, a.k, a.m, a.m.tensor != 0);
     double emax_abs = 0.0, emax_rel = 0.0;
     for (int e = lane; e < n_ent; e += 32) {
-        const uint32_t j = wj[e];
-        double D = INFINITY;
-        if (j != kInvalid && (double)wv[e] <= T) {
-            D = canon_D(xi, a.X + (int64_t)j * a.d, a.d);
-            ++ncand;
-            const double err = fabs((double)wv[e] * a.m.inv_scale2 - D);
+        if (wD[e] < INFINITY) {
+            const double err = fabs((double)wv[e] * a.m.inv_scale2 - wD[e]);
             emax_abs = fmax(emax_abs, err);
-            if (D > 0.0) emax_rel = fmax(emax_rel, err / D);
+            if (wD[e] > 0.0) emax_rel = fmax(emax_rel, err / wD[e]);
         }
-        wD[e] = D;
     }
-    __syncwarp();
     int n_out;
     select_topk(wD, wj, n_ent, a.k, i, a.res_j, a.res_D, &n_out);
-    const int nc = __reduce_add_sync(0xffffffffu, ncand);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         emax_abs = fmax(emax_abs, __shfl_xor_sync(0xffffffffu, emax_abs, o));
@@ -191,24 +248,35 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t p = (int64_t)blockIdx.x * kFinWarps + warp;
     if (p >= a.n) return;
-    const uint32_t i = a.rows[p];
+    const uint32_t i = a.pos2row[a.rows[p]];
     const uint32_t cnt = a.coll_cnt[p];
     if ((int64_t)cnt > a.cap) {
-        if (lane == 0) atomicExch(a.retry_flag, 1);
+        // too many for this pass's capacity: the count is exact, the host re-runs the
+        // row with room for all of them
+        if (lane == 0) {
+            atomicExch(a.retry_flag, 1);
+            a.heavy_idx[atomicAdd(a.heavy_cnt, 1u)] = (uint32_t)(a.heavy_base + p);
+            atomicMax(a.heavy_max, (unsigned long long)cnt);
+        }
         return;
     }
     const float *xi = a.X + (int64_t)i * a.d;
     double *wD = a.scratch_D + p * a.cap;
     uint32_t *wj = const_cast<uint32_t *>(a.coll_j) + p * a.cap;
-    for (uint32_t e = lane; e < cnt; e += 32) wD[e] = canon_D(xi, a.X + (int64_t)wj[e] * a.d, a.d);
+    for (uint32_t e = lane; e < cnt; e += 32) {
+        wj[e] = a.pos2row[wj[e]];   // positions -> original row indices
+        wD[e] = 0.0;
+    }
     __syncwarp();
+    __threadfence_block();
+    const int nd = exact_distances(xi, a.X, a.d, wD, wj, (int)cnt, a.k, a.m, true);
     __threadfence_block();
     int n_out;
     select_topk(wD, wj, (int)cnt, a.k, i, a.res_j, a.res_D, &n_out);
     if (lane == 0) {
         if (a.res_n) a.res_n[i] = (uint8_t)n_out;
         if (a.res_exh) a.res_exh[i] = (uint8_t)((int)cnt < a.k);
-        if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)cnt);
+        if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nd);
         if (a.st_max_cand) atomicMax(a.st_max_cand, (unsigned long long)cnt);
     }
 }
@@ -218,7 +286,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s)
 {
     if (a.nslots <= 0) return cudaSuccess;
-    const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4);   // <= 96 KB
+    const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4);   // <= 160 KB
     cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((a.nslots + kFinWarps - 1) / kFinWarps);

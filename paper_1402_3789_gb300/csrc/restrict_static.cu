@@ -31,6 +31,7 @@ constexpr int64_t kStaticBlocks = (kStaticMaxRows + 255) / 256;
 // block_sums [kStaticBlocks], then two 64-bit counters (n_merges, K)
 constexpr int64_t kWords = 5 * kStaticMaxRows + kStaticBlocks + 4;
 constexpr size_t kStaticBytes = (size_t)kWords * 4;
+static_assert(kStaticBytes < (size_t)24 << 20, "the fixed scratch array stays modest (~21 MB)");
 
 static __device__ __align__(256) uint32_t g_static_scratch[kWords];
 

@@ -108,11 +108,63 @@ __global__ void k_best_ab(RoundState st)
 __global__ void k_flag(RoundState st)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= st.N || st.row_state[i] != 2) return;
-    const uint32_t c = st.comp[i];
-    if (key_less(st.row_D[i], st.row_ab[i], st.best_D[c], st.best_ab[c])) {
-        const uint32_t p = atomicAdd(&st.counters[0], 1u);
-        st.list[p] = (uint32_t)i;
+    if (i >= st.N) return;
+    uint8_t f = 0;
+    if (st.row_state[i] == 2) {
+        const uint32_t c = st.comp[i];
+        f = key_less(st.row_D[i], st.row_ab[i], st.best_D[c], st.best_ab[c]);
+    }
+    st.flag_pos[st.row2pos[i]] = f;
+}
+
+// Rescan rows in increasing position (so that a row tile of a rescan is spatially
+// coherent): per-block counts, a prefix over blocks, then an ordered scatter.
+constexpr int kCompact = 1024;
+
+__global__ void __launch_bounds__(kCompact) k_compact_count(RoundState st)
+{
+    const int64_t p = (int64_t)blockIdx.x * kCompact + threadIdx.x;
+    const int f = p < st.N ? st.flag_pos[p] : 0;
+    const int c = __syncthreads_count(f);
+    if (threadIdx.x == 0) st.block_cnt[blockIdx.x] = (uint32_t)c;
+}
+
+__global__ void k_compact_prefix(RoundState st, int64_t nb)
+{
+    if (threadIdx.x != 0) return;
+    uint32_t run = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const uint32_t v = st.block_cnt[b];
+        st.block_cnt[b] = run;
+        run += v;
+    }
+    st.counters[0] = run;
+}
+
+__global__ void __launch_bounds__(kCompact) k_compact_scatter(RoundState st)
+{
+    __shared__ uint32_t ws[kCompact / 32];
+    const int64_t p = (int64_t)blockIdx.x * kCompact + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t f = p < st.N ? st.flag_pos[p] : 0u;
+    const uint32_t bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) ws[w] = __popc(bal);
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t v = ws[lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        ws[lane] = x - v;
+    }
+    __syncthreads();
+    if (f) {
+        const uint32_t r = st.block_cnt[blockIdx.x] + ws[w] + __popc(bal & ((1u << lane) - 1u));
+        st.list_pos[r] = (uint32_t)p;
+        st.list[r] = st.pos2row[p];
     }
 }
 
@@ -193,7 +245,11 @@ cudaError_t launch_component_min(RoundState &st, cudaStream_t s)
 cudaError_t launch_flag_rescans(RoundState &st, cudaStream_t s)
 {
     k_flag<<<grid_for(st.N), kThreads, 0, s>>>(st);
-    count_launches(1);
+    const int64_t nb = (st.N + kCompact - 1) / kCompact;
+    k_compact_count<<<(unsigned)nb, kCompact, 0, s>>>(st);
+    k_compact_prefix<<<1, 32, 0, s>>>(st, nb);
+    k_compact_scatter<<<(unsigned)nb, kCompact, 0, s>>>(st);
+    count_launches(4);
     return cudaGetLastError();
 }
 

@@ -4,8 +4,8 @@
 // T(v_k), where v_k is the k-th smallest value and T the proven error bound around it
 // (see rerank.cu).  A sweep therefore keeps, per row and column range:
 //   - the KC smallest values seen so far, sorted, in registers (KC >= k), and
-//   - a "band" of up to kBand further values that are still <= T(current KC-th),
-//     in shared memory.
+//   - a "band" of up to CB further values that are still <= T(current KC-th), in
+//     shared memory (CB is chosen per kernel: narrow for FP32, wide for 16-bit).
 // The fast-path threshold of the row is T(current KC-th value): it only falls, so a
 // value above it can never be needed.  When the band is full it is compacted against
 // the current threshold; if it is still full the row is flagged (the re-rank then sends
@@ -17,9 +17,8 @@
 
 namespace nnm {
 
-constexpr int kTop = 16;    // register slots per row in the output record
-constexpr int kBand = 32;   // band slots per row
-static_assert(kTop + kBand == kListC, "record layout");
+constexpr int kTop = 16;                    // register slots per row in the output record
+constexpr int kBandMax = kListC - kTop;     // band slots per row in the output record
 
 // Per-row constants (tensor path): eps = gamma (P_i + Pmax)^2 + E_i + Emax, rr = r_i + R.
 struct RowConst {
@@ -51,11 +50,12 @@ __device__ __forceinline__ float sel_threshold(const SelConst &c, const RowConst
 
 // Append (v, j) to a row's band (entry m at bv[m * stride]); when it is full, first
 // drop the entries above thr.  Returns the new count, or -1 if it is still full.
-static __device__ __noinline__ int band_push(float v, uint32_t j, int bcnt, float thr, float *bv, uint32_t *bj, int stride)
+static __device__ __noinline__ int band_push(float v, uint32_t j, int bcnt, int cap, float thr, float *bv, uint32_t *bj,
+                                             int stride)
 {
-    if (bcnt == kBand) {
+    if (bcnt == cap) {
         int w = 0;
-        for (int m = 0; m < kBand; ++m) {
+        for (int m = 0; m < cap; ++m) {
             const float x = bv[m * stride];
             if (x <= thr) {
                 bv[w * stride] = x;
@@ -64,15 +64,16 @@ static __device__ __noinline__ int band_push(float v, uint32_t j, int bcnt, floa
             }
         }
         bcnt = w;
-        if (bcnt == kBand) return -1;
+        if (bcnt == cap) return -1;
     }
     bv[bcnt * stride] = v;
     bj[bcnt * stride] = j;
     return bcnt + 1;
 }
 
-template <int KC>
+template <int KC, int CB>
 struct RowSel {
+    static_assert(CB <= kBandMax, "band larger than the output record");
     float tv[KC];
     uint32_t tj[KC];
     float thr;   // values >= thr (strictly above T) are never needed
@@ -117,7 +118,7 @@ struct RowSel {
 
     __device__ __forceinline__ void push(float v, uint32_t j, float *bv, uint32_t *bj, int stride)
     {
-        const int r = band_push(v, j, bcnt, thr, bv, bj, stride);
+        const int r = band_push(v, j, bcnt, CB, thr, bv, bj, stride);
         if (r < 0) {
             bovf = 1;
             thr = -INFINITY;   // flagged: nothing more is needed from this sweep
@@ -126,7 +127,8 @@ struct RowSel {
         }
     }
 
-    // Output record: kTop top slots (KC used), kBand band slots; ovf flag separately.
+    // Output record: kTop top slots (KC used), kBandMax band slots (CB used); overflow
+    // flag separately.
     __device__ __forceinline__ void write(float *ov, uint32_t *oj, uint8_t *oflag, const float *bv, const uint32_t *bj,
                                           int stride)
     {
@@ -135,7 +137,7 @@ struct RowSel {
             ov[m] = m < KC ? tv[m < KC ? m : 0] : INFINITY;
             oj[m] = m < KC ? tj[m < KC ? m : 0] : kInvalid;
         }
-        for (int m = 0; m < kBand; ++m) {
+        for (int m = 0; m < kBandMax; ++m) {
             const bool ok = m < bcnt && !bovf;
             ov[kTop + m] = ok ? bv[m * stride] : INFINITY;
             oj[kTop + m] = ok ? bj[m * stride] : kInvalid;

@@ -25,6 +25,7 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kTile = 64;   // columns per shared-memory tile
+constexpr int kBand = 32;   // band slots per row (the FP32 band is narrow)
 
 template <int D, int KC, bool COLLECT>
 __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
@@ -41,13 +42,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     uint32_t row[2], crow[2];
     float x[2][D];
     float cthr[2];
-    RowSel<KC> sel[2];
+    RowSel<KC, kBand> sel[2];
     const RowConst rc{0.f, 0.f};
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
         valid[r] = slot[r] < a.nslots;
-        row[r] = valid[r] ? (a.rows ? a.rows[slot[r]] : (uint32_t)slot[r]) : 0u;
-        crow[r] = (valid[r] && a.comp) ? a.comp[row[r]] : 0u;
+        row[r] = valid[r] ? (a.rows ? a.rows[slot[r]] : (uint32_t)slot[r]) : 0u;   // position
+        crow[r] = (valid[r] && a.comp) ? a.comp[a.pos2row[row[r]]] : 0u;
         const float *xr = a.Xs + (int64_t)row[r] * a.dp;
 #pragma unroll
         for (int k = 0; k < D; ++k) x[r][k] = k < a.dp ? xr[k] : 0.0f;
@@ -55,19 +56,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
         sel[r].init(valid[r]);
     }
 
+    // Column tiles in the order of the operands, starting at this row tile's own place and
+    // wrapping around (near neighbours first); split s takes the s-th range of that order.
     const int split = blockIdx.y;
-    const int64_t cb = a.col_begin + (int64_t)split * a.cols_per_split;
-    int64_t ce = cb + a.cols_per_split;
-    if (ce > a.col_end) ce = a.col_end;
-    const int64_t ntiles = ce > cb ? (ce - cb + kTile - 1) / kTile : 0;
+    const int64_t ntile_all = (a.N + kTile - 1) / kTile;
+    const int64_t tile0 = (int64_t)(a.rows ? a.rows[(int64_t)blockIdx.x * kRowTile] : (uint32_t)(blockIdx.x * kRowTile)) /
+                          kTile;
+    const int64_t tps = a.cols_per_split / kTile;
+    const int64_t t_begin = (int64_t)split * tps;
+    const int64_t t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
+    const int64_t ntiles = t_end > t_begin ? t_end - t_begin : 0;
+    auto tile_col = [&](int64_t tile) -> int64_t { return ((tile0 + t_begin + tile) % ntile_all) * kTile; };
 
     // operand rows hold a.dp floats; the tile keeps DP >= a.dp per column (rest zero)
     if (a.dp < DP)
         for (int q = t; q < 2 * kTile * DP; q += kThreads) (&sy[0][0])[q] = 0.0f;
     __syncthreads();
     auto load_tile = [&](int64_t tile, int buf) {
-        const int64_t j0 = cb + tile * kTile;
-        int64_t n = ce - j0;
+        const int64_t j0 = tile_col(tile);
+        int64_t n = a.N - j0;
         if (n > kTile) n = kTile;
         const int per = a.dp / 4;
         const int chunks = (int)n * per;
@@ -79,8 +86,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     };
 
     auto consider = [&](int r, float v, uint32_t j) {
-        if ((int64_t)j >= ce || j == row[r]) return;
-        if (a.comp && a.comp[j] == crow[r]) return;
+        if ((int64_t)j >= a.N || j == row[r]) return;
+        if (a.comp && a.comp[a.pos2row[j]] == crow[r]) return;
         if (COLLECT) {
             if (!(v <= cthr[r])) return;
             const uint32_t p = atomicAdd(&a.coll_cnt[slot[r]], 1u);
@@ -99,8 +106,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
         __pipeline_wait_prior(1);
         __syncthreads();
         const float *ys = sy[tile & 1];
-        const int64_t j0 = cb + tile * kTile;
-        const int n = (int)(ce - j0 < kTile ? ce - j0 : kTile);
+        const int64_t j0 = tile_col(tile);
+        const int n = (int)(a.N - j0 < kTile ? a.N - j0 : kTile);
         float th0 = COLLECT ? cthr[0] : sel[0].thr;
         float th1 = COLLECT ? cthr[1] : sel[1].thr;
         for (int c = 0; c < n; c += 2) {

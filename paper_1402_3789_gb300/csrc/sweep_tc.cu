@@ -29,6 +29,7 @@ constexpr int kMmaWarp = 8;
 constexpr int kProdWarp = 9;
 constexpr int kBN = 128;          // columns per B tile
 constexpr int kMaxStages = 8;
+constexpr int kBandWide = 64;   // band slots per row for one-term BF16 (a wide band)
 constexpr int kStageStride = 36;   // floats per thread in the hit-staging area (16-byte rows, no bank conflicts)
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
 
@@ -177,12 +178,6 @@ __device__ __forceinline__ void reg_fence(uint32_t (&v)[32])
                  : "memory");
 }
 
-__device__ __forceinline__ float min3f(float a, float b, float c)
-{
-    float r;
-    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-    return r;
-}
 
 struct __align__(8) TcShared {
     uint64_t full[kMaxStages];
@@ -195,37 +190,43 @@ struct __align__(8) TcShared {
 };
 
 // Shared-memory stages of the B ring that fit next to the other regions.
-__host__ __device__ inline int tc_stages(int kpad)
+__host__ __device__ inline int tc_stages(int kpad, int band)
 {
-    const size_t fixed = (size_t)kRowTile * kpad * 2 + 256 + (size_t)kBand * kRowTile * 8 +
+    const size_t fixed = (size_t)kRowTile * kpad * 2 + 256 + (size_t)band * kRowTile * 8 +
                          (size_t)kRowTile * kStageStride * 4 + 1024;
     const size_t per = (size_t)kBN * kpad * 2;
     int s = (int)((225 * 1024 - fixed) / per);
     return s > kMaxStages ? kMaxStages : s;
 }
 
-template <int KC, bool COLLECT>
+template <int KC, int CB, bool COLLECT>
 __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const int kpad = a.kpad;
-    const int kStages = tc_stages(kpad);
+    const int kStages = tc_stages(kpad, CB);
     const uint32_t a_bytes = (uint32_t)kRowTile * kpad * 2;
     const uint32_t b_bytes = (uint32_t)kBN * kpad * 2;
     uint8_t *sA = smem_raw;
     uint8_t *sB = smem_raw + a_bytes;
     TcShared *sh = reinterpret_cast<TcShared *>(sB + (size_t)kStages * b_bytes);
-    float *band_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(sh) + 256);   // [kBand][256]
-    uint32_t *band_j = reinterpret_cast<uint32_t *>(band_v + kBand * kRowTile);
-    float *stage_v = reinterpret_cast<float *>(band_j + kBand * kRowTile);               // [256][kStageStride]
+    float *band_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(sh) + 256);   // [CB][256]
+    uint32_t *band_j = reinterpret_cast<uint32_t *>(band_v + CB * kRowTile);
+    float *stage_v = reinterpret_cast<float *>(band_j + CB * kRowTile);                  // [256][kStageStride]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
-    const int64_t cb = a.col_begin + (int64_t)split * a.cols_per_split;
-    int64_t ce = cb + a.cols_per_split;
-    if (ce > a.col_end) ce = a.col_end;
-    const int ntiles = ce > cb ? (int)((ce - cb + kBN - 1) / kBN) : 0;
     const int64_t slot0 = (int64_t)blockIdx.x * kRowTile;
+    // Column tiles in the order of the operands, starting at this row tile's own place
+    // and wrapping around: near neighbours come first, so thresholds fall early.  Split
+    // s takes the s-th range of that cyclic order.
+    const int64_t ntile_all = (a.N + kBN - 1) / kBN;
+    const int64_t tile0 = (int64_t)(a.rows ? a.rows[slot0] : (uint32_t)slot0) / kBN;
+    const int64_t tps = a.cols_per_split / kBN;
+    const int64_t t_begin = (int64_t)split * tps;
+    const int64_t t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
+    const int ntiles = t_end > t_begin ? (int)(t_end - t_begin) : 0;
+    auto tile_col = [&](int t) -> int64_t { return ((tile0 + t_begin + t) % ntile_all) * kBN; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -258,8 +259,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         uint4 *dst = reinterpret_cast<uint4 *>(sA);
         if (slot < a.nslots) {
             myrow_slot = r;
-            myrow = a.rows ? a.rows[slot] : (uint32_t)slot;
-            mycomp = a.comp ? a.comp[myrow] : 0u;
+            myrow = a.rows ? a.rows[slot] : (uint32_t)slot;   // position
+            mycomp = a.comp ? a.comp[a.pos2row[myrow]] : 0u;
             const uint4 *src = reinterpret_cast<const uint4 *>(a.XA);
             for (int c = 0; c < chunks; ++c)
                 dst[((r >> 3) * chunks + c) * 8 + (r & 7)] = src[(((int64_t)myrow >> 3) * chunks + c) * 8 + (myrow & 7)];
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             if (lane == 0) {
                 mbar_arrive_expect_tx(&sh->full[s], b_bytes);
-                const int64_t col = cb + (int64_t)t * kBN;
+                const int64_t col = tile_col(t);
                 bulk_g2s(sB + (size_t)s * b_bytes, a.XB + col * kpad, b_bytes, &sh->full[s]);
             }
             issued = t + 1;
@@ -350,9 +351,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         const int half = warp >> 2, quad = warp & 3;
         const bool valid = myrow_slot >= 0;
         const float cthr = (COLLECT && valid) ? a.thr[slot0 + myrow_slot] : -INFINITY;
-        RowSel<KC> sel;
+        RowSel<KC, CB> sel;
         sel.init(valid);
-        const RowConst rc = valid ? make_rowconst(a.sc, a.m, myrow) : RowConst{0.f, 0.f};
+        const RowConst rc = valid ? make_rowconst(a.sc, a.m, a.pos2row[myrow]) : RowConst{0.f, 0.f};
         float *bv = band_v + threadIdx.x;
         uint32_t *bj = band_j + threadIdx.x;
         float *stg = stage_v + threadIdx.x * kStageStride;
@@ -386,8 +387,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 const float val = stg[q];
                 const int64_t j = jbase + q;
                 if (!(val <= (COLLECT ? cthr : sel.thr))) continue;
-                if (j >= ce || (uint32_t)j == myrow) continue;
-                if (a.comp && a.comp[j] == mycomp) continue;
+                if (j >= a.N || (uint32_t)j == myrow) continue;
+                if (a.comp && a.comp[a.pos2row[j]] == mycomp) continue;
                 if (COLLECT) {
                     const int64_t sl = slot0 + myrow_slot;
                     const uint32_t p = atomicAdd(&a.coll_cnt[sl], 1u);
@@ -407,7 +408,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 break;
             }
             tc_fence_after();
-            const int64_t col0 = cb + (int64_t)t * kBN;
+            const int64_t col0 = tile_col(t);
             const uint32_t taddr = lane_base + (uint32_t)((b * 2 + half) * kBN);
 #pragma unroll 1
             for (int hh = 0; hh < kBN / 64; ++hh) {
@@ -448,35 +449,44 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
 
 }  // namespace
 
-size_t sweep_tc_smem_bytes(int kpad)
+size_t sweep_tc_smem_bytes(int kpad, int band)
 {
     // at least ~half of the SM's shared memory keeps one CTA per SM (it holds all of TMEM)
-    const size_t need = (size_t)kRowTile * kpad * 2 + (size_t)tc_stages(kpad) * kBN * kpad * 2 + 256 +
-                        (size_t)kBand * kRowTile * 8 + (size_t)kRowTile * kStageStride * 4 + 1024;
+    const size_t need = (size_t)kRowTile * kpad * 2 + (size_t)tc_stages(kpad, band) * kBN * kpad * 2 + 256 +
+                        (size_t)band * kRowTile * 8 + (size_t)kRowTile * kStageStride * 4 + 1024;
     const size_t one_per_sm = 120 * 1024;
     return need > one_per_sm ? need : one_per_sm;
 }
 
-template <int KC, bool COLL>
+template <int KC, int CB, bool COLL>
 static cudaError_t go_tc(const SweepArgs &a, dim3 grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_tc<KC, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_sweep_tc<KC, CB, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_sweep_tc<KC, COLL><<<grid, kThreadsTc, smem, s>>>(a);
+    k_sweep_tc<KC, CB, COLL><<<grid, kThreadsTc, smem, s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
 
+template <int CB>
+static cudaError_t go_tc_band(const SweepArgs &a, bool collect, dim3 grid, cudaStream_t s)
+{
+    const size_t smem = sweep_tc_smem_bytes(a.kpad, CB);
+    if (tc_stages(a.kpad, CB) < 2) return cudaErrorInvalidValue;
+    if (collect) return go_tc<1, CB, true>(a, grid, smem, s);
+    if (a.kc <= 1) return go_tc<1, CB, false>(a, grid, smem, s);
+    if (a.kc <= 2) return go_tc<2, CB, false>(a, grid, smem, s);
+    if (a.kc <= 4) return go_tc<4, CB, false>(a, grid, smem, s);
+    if (a.kc <= 8) return go_tc<8, CB, false>(a, grid, smem, s);
+    return go_tc<16, CB, false>(a, grid, smem, s);
+}
+
 cudaError_t launch_sweep_tc(const SweepArgs &a, bool collect, cudaStream_t s)
 {
-    const size_t smem = sweep_tc_smem_bytes(a.kpad);
     dim3 grid((unsigned)((a.nslots + kRowTile - 1) / kRowTile), (unsigned)a.splits);
-    if (collect) return go_tc<1, true>(a, grid, smem, s);
-    if (a.kc <= 1) return go_tc<1, false>(a, grid, smem, s);
-    if (a.kc <= 2) return go_tc<2, false>(a, grid, smem, s);
-    if (a.kc <= 4) return go_tc<4, false>(a, grid, smem, s);
-    if (a.kc <= 8) return go_tc<8, false>(a, grid, smem, s);
-    return go_tc<16, false>(a, grid, smem, s);
+    if (a.band > 32) return go_tc_band<kBandWide>(a, collect, grid, s);
+    return go_tc_band<32>(a, collect, grid, s);
 }
 
 }  // namespace nnm

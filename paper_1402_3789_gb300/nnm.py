@@ -24,7 +24,7 @@ import torch
 from . import build as _build
 
 NNM_OK, NNM_EINVAL, NNM_ENONFINITE, NNM_ENOMEM, NNM_ECUDA, NNM_ETIMEOUT, NNM_EUNSUPPORTED = range(7)
-PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2}
+PRECISIONS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16x3": 3}
 
 EDGE_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("D", "<f8")])
 MERGE_DTYPE = np.dtype([("a", "<u4"), ("b", "<u4"), ("D", "<f8"), ("dist", "<f8"), ("new_size", "<i8")])

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-PRECISIONS = ["fp32", "bf16", "fp16"]
+PRECISIONS = ["fp32", "bf16", "fp16", "bf16x3"]
 
 
 @pytest.fixture(scope="module")
@@ -69,6 +69,8 @@ def run_cluster(nnm, X, restr, precision, **opt):
 @pytest.mark.parametrize("n,d,k", [(4096, 8, 1), (4096, 8, 8), (3001, 25, 5), (777, 3, 16), (300, 32, 2),
                                    (1000, 1, 4), (5000, 16, 12)])
 def test_nearest_matches_oracle(nnm, orc, precision, n, d, k):
+    if precision == "bf16x3" and d > 30:
+        pytest.skip("the split form takes d <= 30")
     rng = np.random.default_rng(n + d)
     X = (rng.standard_normal((n, d)) * rng.uniform(0.5, 3, d) + rng.integers(0, 5, (n, 1))).astype(np.float32)
     idx, D, st = run_nearest(nnm, X, k, precision)
@@ -104,7 +106,7 @@ def test_nearest_all_identical_rows(nnm, orc, precision):
     assert np.array_equal(idx, oi) and np.array_equal(D, oD)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("precision", ["bf16", "fp16", "bf16x3"])
 def test_nearest_large_offset_and_spread(nnm, orc, precision):
     # large common offset (removed by centring) and features of very different scale:
     # the rounding radii are large, so the completeness test does real work
@@ -150,7 +152,7 @@ RESTRICTIONS = [
 ]
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
 @pytest.mark.parametrize("restr", RESTRICTIONS, ids=[str(i) for i in range(len(RESTRICTIONS))])
 def test_cluster_restrictions(nnm, orc, precision, restr):
     X = make("nnm_n4096_d8", 5000, seed=11)
@@ -209,6 +211,9 @@ def test_cluster_mixture_n20000(nnm, orc, precision):
 
 def test_errors(nnm):
     X = np.random.default_rng(0).standard_normal((100, 4)).astype(np.float32)
+    with pytest.raises(nnm.NNMError) as e:
+        nnm.nnm_create(dev(np.zeros((10, 31), np.float32)), precision="bf16x3")
+    assert e.value.status == nnm.NNM_EUNSUPPORTED
     Xbad = X.copy()
     Xbad[7, 2] = np.nan
     with pytest.raises(nnm.NNMError) as e:
@@ -248,5 +253,5 @@ def test_candidates_are_tight(nnm, precision):
     _, _, st = run_nearest(nnm, X, 4, precision)
     assert st["rows_overflowed"] == 0
     assert st["rerank_pairs"] <= 12 * 4096
-    bound = {"fp32": 10 * 2.0 ** -24, "fp16": 0.05, "bf16": 0.25}[precision]
+    bound = {"fp32": 10 * 2.0 ** -24, "fp16": 0.05, "bf16": 0.25, "bf16x3": 0.01}[precision]
     assert st["max_rel_err"] <= bound
