@@ -288,6 +288,7 @@ def run_ours(args, world, rank, local):
             "rounds": stats[-1]["rounds"], "rows_rescanned": stats[-1]["rows_rescanned"],
             "rows_overflowed": stats[-1]["rows_overflowed"], "rerank_pairs": stats[-1]["rerank_pairs"],
             "max_candidates_per_row": stats[-1]["max_candidates"],
+            "tiles_skipped": stats[-1]["tiles_skipped"], "tiles_swept": stats[-1]["tiles_swept"],
             "max_abs_err_vs_fp64": max(s["max_abs_err"] for s in stats),
             "max_rel_err_vs_fp64": max(s["max_rel_err"] for s in stats),
             "n_merges": last.n_merges, "n_clusters": last.n_clusters,

@@ -75,7 +75,8 @@ typedef struct {
                               (the restricted result is unchanged; the merge tree returned
                               by nnm_get_tree then holds only edges within the cap)        */
     int32_t col_split;     /* 0: automatic; >0: number of column ranges per row tile      */
-    int32_t reserved;
+    int32_t no_tile_pruning; /* 1: evaluate every column tile (no bounding-sphere skipping;
+                                results are identical, only slower)                        */
 } nnm_options;
 
 /* Restrictions ("Problem statement"; "Problem settings").  Zero disables each one.
@@ -142,6 +143,8 @@ typedef struct {
     int32_t cache_k;         /* cached neighbours per row                          */
     double scale;            /* power-of-two operand scale (tensor paths)          */
     int64_t kernel_launches; /* kernels this library launched during the call      */
+    int64_t tiles_skipped;   /* column tiles skipped by the bounding-sphere bound   */
+    int64_t tiles_swept;     /* column tiles evaluated                              */
 } nnm_stats;
 
 /* nnm_create -- "main module" ("Objectives of the main module"): validate the data

@@ -45,8 +45,11 @@ struct nnm_ctx {
     double scale = 1.0;
     Margin margin{};
     SelConst selc{};
-    // spatial order of the operands (see prep.cu)
+    // spatial order of the operands (see prep.cu) and the column tiles' bounding spheres
     uint32_t *pos2row = nullptr, *row2pos = nullptr, *list_pos = nullptr;
+    float *tile_c = nullptr, *tile_rho = nullptr, *mu_f = nullptr;
+    int tile_w = 0;
+    float lb_R2 = 0.f, lb_eps = 0.f, lb_gamma = 0.f;
     // operands
     float *Xs = nullptr;
     uint16_t *XA = nullptr, *XB = nullptr;
@@ -56,13 +59,16 @@ struct nnm_ctx {
     uint32_t *cand_j = nullptr;
     uint8_t *cand_ovf = nullptr;
     size_t cand_cap = 0;         // records (one per row slot and column range)
-    uint32_t *ovf_row = nullptr;
-    float *ovf_thr = nullptr;
+    uint32_t *ovf_row = nullptr, *ovf_blk = nullptr;
+    float *ovf_thr = nullptr, *ovf_thr_slot = nullptr;
+    uint8_t *ovf_flag = nullptr;
+    unsigned int *slot_thr = nullptr;
     size_t ovf_cap = 0;          // slots
     uint32_t *coll_cnt = nullptr, *coll_j = nullptr;
     double *coll_D = nullptr;
     size_t coll_cap = 0;         // entries
-    uint32_t *heavy_idx = nullptr, *heavy_rows = nullptr, *heavy_rows2 = nullptr;
+    uint8_t *heavy_flag = nullptr;
+    uint32_t *heavy_blk = nullptr, *heavy_rows = nullptr, *heavy_rows2 = nullptr;
     float *heavy_thr = nullptr, *heavy_thr2 = nullptr;
     size_t heavy_cap = 0;        // rows
     // cache and rounds
@@ -225,7 +231,11 @@ nnm_status ensure_ovf(nnm_ctx *c, size_t slots)
     if (slots <= c->ovf_cap) return NNM_OK;
     NNM_TRY(dalloc(c, &c->ovf_row, slots));
     NNM_TRY(dalloc(c, &c->ovf_thr, slots));
+    NNM_TRY(dalloc(c, &c->ovf_thr_slot, slots));
+    NNM_TRY(dalloc(c, &c->ovf_flag, slots));
+    NNM_TRY(dalloc(c, &c->ovf_blk, (size_t)compact_blocks((int64_t)slots)));
     NNM_TRY(dalloc(c, &c->coll_cnt, slots));
+    NNM_TRY(dalloc(c, &c->slot_thr, slots));
     c->ovf_cap = slots;
     return NNM_OK;
 }
@@ -233,7 +243,8 @@ nnm_status ensure_ovf(nnm_ctx *c, size_t slots)
 nnm_status ensure_heavy(nnm_ctx *c, size_t rows)
 {
     if (rows <= c->heavy_cap) return NNM_OK;
-    NNM_TRY(dalloc(c, &c->heavy_idx, rows));
+    NNM_TRY(dalloc(c, &c->heavy_flag, rows));
+    NNM_TRY(dalloc(c, &c->heavy_blk, (size_t)compact_blocks((int64_t)rows)));
     NNM_TRY(dalloc(c, &c->heavy_rows, rows));
     NNM_TRY(dalloc(c, &c->heavy_rows2, rows));
     NNM_TRY(dalloc(c, &c->heavy_thr, rows));
@@ -266,6 +277,18 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.col_end = c->N;
     a.pos2row = c->pos2row;
     a.err_flag = &c->derr[0];
+    a.prune = c->opt.no_tile_pruning ? 0 : 1;
+    a.tile_w = c->tile_w;
+    a.tile_c = c->tile_c;
+    a.tile_rho = c->tile_rho;
+    a.mu_f = c->mu_f;
+    a.scale_f = (float)c->scale;
+    a.lb_R2 = c->lb_R2;
+    a.lb_eps = c->lb_eps;
+    a.lb_gamma = c->lb_gamma;
+    a.X = c->X;
+    a.d = c->d;
+    a.st_tiles = &c->dstat[13];
     a.m = c->margin;
     a.sc = c->selc;
     a.kc = 1;
@@ -312,7 +335,6 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
         if (batch < 1) batch = 1;
         if (batch > n) batch = n;
         NNM_TRY(ensure_coll(c, (size_t)batch * cap));
-        NNM_CUDA(c, cudaMemsetAsync(&c->dcount[5], 0, sizeof(uint32_t), s));
         NNM_CUDA(c, cudaMemsetAsync(&c->dstat[12], 0, sizeof(unsigned long long), s));
         for (int64_t b0 = 0; b0 < n; b0 += batch) {
             const int64_t nb = n - b0 < batch ? n - b0 : batch;
@@ -352,14 +374,16 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
             ra.res_n = res_n;
             ra.res_exh = res_exh;
             ra.retry_flag = &c->derr[1];
-            ra.heavy_cnt = &c->dcount[5];
-            ra.heavy_idx = c->heavy_idx;
+            ra.heavy_flag = c->heavy_flag;
             ra.heavy_base = b0;
             ra.heavy_max = &c->dstat[12];
             ra.st_pairs = &c->dstat[2];
             ra.st_max_cand = &c->dstat[3];
             NNM_CUDA(c, launch_collect_rerank(ra, s));
         }
+        // heavy rows in collect-slot order (the order of the rows, hence spatial)
+        NNM_CUDA(c, launch_compact(c->heavy_flag, n, rows, thr, c->heavy_blk, c->heavy_rows, c->heavy_thr,
+                                   &c->dcount[5], s));
         uint32_t nheavy = 0;
         unsigned long long hmax = 0;
         NNM_CUDA(c, cudaMemcpyAsync(&nheavy, &c->dcount[5], sizeof nheavy, cudaMemcpyDeviceToHost, s));
@@ -367,9 +391,6 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
         NNM_CUDA(c, cudaStreamSynchronize(s));
         if (nheavy == 0) break;
         // the next pass runs only the heavy rows, with room for the largest exact count
-        NNM_CUDA(c, launch_gather_u32(c->heavy_idx, rows, nheavy, c->heavy_rows, s));
-        NNM_CUDA(c, launch_gather_f32(c->heavy_idx, thr, nheavy, c->heavy_thr, s));
-        NNM_CUDA(c, cudaStreamSynchronize(s));
         // swap: the gathered lists become this function's inputs
         std::swap(c->heavy_rows, c->heavy_rows2);
         std::swap(c->heavy_thr, c->heavy_thr2);
@@ -404,6 +425,8 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     sa.out_j = c->cand_j;
     sa.out_ovf = c->cand_ovf;
     sa.kc = k;
+    sa.slot_thr = c->slot_thr;
+    if (splits > 1) NNM_CUDA(c, cudaMemsetAsync(c->slot_thr, 0xFF, (size_t)nslots * sizeof(unsigned int), c->stream));
     {
         Phase ph(c, &c->stats.ms_sweep);
         if (full) NNM_CUDA(c, cudaEventRecord(c->ev0, c->stream));
@@ -421,7 +444,6 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     uint32_t novf = 0;
     {
         Phase ph(c, &c->stats.ms_rerank);
-        NNM_CUDA(c, cudaMemsetAsync(&c->dcount[0], 0, sizeof(uint32_t), c->stream));
         FinalizeArgs fa{};
         fa.X = c->X;
         fa.d = c->d;
@@ -439,14 +461,16 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
         fa.res_D = res_D;
         fa.res_n = res_n;
         fa.res_exh = res_exh;
-        fa.ovf_cnt = &c->dcount[0];
-        fa.ovf_row = c->ovf_row;
-        fa.ovf_thr = c->ovf_thr;
+        fa.ovf_flag = c->ovf_flag;
+        fa.ovf_thr = c->ovf_thr_slot;
         fa.st_max_abs = &c->dstat[0];
         fa.st_max_rel = &c->dstat[1];
         fa.st_pairs = &c->dstat[2];
         fa.st_max_cand = &c->dstat[3];
         NNM_CUDA(c, launch_finalize(fa, c->stream));
+        // incomplete rows in slot order, so that the collect pass keeps the spatial order
+        NNM_CUDA(c, launch_compact(c->ovf_flag, nslots, rows, c->ovf_thr_slot, c->ovf_blk, c->ovf_row, c->ovf_thr,
+                                   &c->dcount[0], c->stream));
         NNM_CUDA(c, cudaMemcpyAsync(&novf, &c->dcount[0], sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
     }
     if (novf == 0) return NNM_OK;
@@ -472,12 +496,14 @@ void reset_stats(nnm_ctx *c)
     c->stats.cache_k = c->kc;
     c->launch_base = launches_so_far();
     cudaMemsetAsync(c->dstat, 0, 4 * sizeof(unsigned long long), c->stream);
+    cudaMemsetAsync(&c->dstat[13], 0, 2 * sizeof(unsigned long long), c->stream);
 }
 
 nnm_status read_stats(nnm_ctx *c)
 {
-    unsigned long long h[4];
+    unsigned long long h[4], ht[2];
     NNM_CUDA(c, cudaMemcpyAsync(h, c->dstat, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    NNM_CUDA(c, cudaMemcpyAsync(ht, &c->dstat[13], sizeof ht, cudaMemcpyDeviceToHost, c->stream));
     NNM_CUDA(c, cudaStreamSynchronize(c->stream));
     double a, r;
     memcpy(&a, &h[0], 8);
@@ -487,6 +513,8 @@ nnm_status read_stats(nnm_ctx *c)
     c->stats.rerank_pairs = (int64_t)h[2];
     c->stats.max_candidates = (int64_t)h[3];
     c->stats.kernel_launches = launches_so_far() - c->launch_base;
+    c->stats.tiles_skipped = (int64_t)ht[0];
+    c->stats.tiles_swept = (int64_t)ht[1];
     return NNM_OK;
 }
 
@@ -519,17 +547,23 @@ nnm_status prepare(nnm_ctx *c)
         int64_t L = c->N / 256;
         if (L > 1024) L = 1024;
         if (L < 1) L = 1;
-        NNM_CUDA(c, launch_landmark_keys(c->X, c->N, c->d, L, keys, s));
+        uint32_t *rank = nullptr;
+        NNM_TRY(dalloc(c, &rank, (size_t)L));
+        NNM_CUDA(c, launch_landmark_chain(c->X, c->N, c->d, L, rank, s));
+        NNM_CUDA(c, launch_landmark_keys(c->X, c->N, c->d, L, rank, keys, s));
         NNM_CUDA(c, launch_sort_edges(keys, tmp, c->N, s, &sorted));
         NNM_CUDA(c, launch_order_from_keys(sorted, c->N, c->pos2row, c->row2pos, s));
         NNM_CUDA(c, cudaStreamSynchronize(s));
         cudaFree(keys);
         cudaFree(tmp);
+        cudaFree(rank);
     }
     if (!is_tensor(c)) {
         c->dp = (c->d + 3) & ~3;
         NNM_TRY(dalloc(c, &c->Xs, (size_t)c->Npad * c->dp));
         NNM_CUDA(c, launch_pad_fp32(c->X, c->N, c->d, c->dp, c->Npad, c->pos2row, c->Xs, s));
+        c->tile_w = 64;
+        c->scale = 1.0;
         const double u = 0x1p-24;
         c->margin.tensor = 0;
         c->margin.gamma = (c->d + 2) * u / (1.0 - (c->d + 2) * u);
@@ -563,9 +597,17 @@ nnm_status prepare(nnm_ctx *c)
                                        c->XB, c->r, c->P, c->E, &c->dstat[9], s));
         unsigned long long mx[3];
         NNM_CUDA(c, cudaMemcpyAsync(mx, &c->dstat[9], sizeof mx, cudaMemcpyDeviceToHost, s));
+        double mu_h[32];
+        float muf_h[32];
+        NNM_CUDA(c, cudaMemcpyAsync(mu_h, mu, c->d * sizeof(double), cudaMemcpyDeviceToHost, s));
+        NNM_CUDA(c, cudaStreamSynchronize(s));
+        for (int k = 0; k < c->d; ++k) muf_h[k] = (float)mu_h[k];
+        NNM_TRY(dalloc(c, &c->mu_f, (size_t)c->d));
+        NNM_CUDA(c, cudaMemcpyAsync(c->mu_f, muf_h, c->d * sizeof(float), cudaMemcpyHostToDevice, s));
         NNM_CUDA(c, cudaStreamSynchronize(s));
         cudaFree(partial);
         cudaFree(mu);
+        c->tile_w = 128;
         c->margin.tensor = 1;
         // FP32 accumulation of kpad exact products, order and rounding mode unknown:
         // at most kpad additions, each off by < 2^-23 of the partial-sum magnitude
@@ -585,6 +627,24 @@ nnm_status prepare(nnm_ctx *c)
         const double u = 0x1p-24;
         c->margin.gamma32 = (c->d + 2) * u / (1.0 - (c->d + 2) * u);
         c->margin.alpha32 = (c->d + 2) * 0x1p-149;
+    }
+    // bounding spheres of the column tiles and the constants of their lower bound
+    {
+        const int64_t nt = (c->N + c->tile_w - 1) / c->tile_w;
+        NNM_TRY(dalloc(c, &c->tile_c, (size_t)nt * c->d));
+        NNM_TRY(dalloc(c, &c->tile_rho, (size_t)nt));
+        NNM_CUDA(c, launch_tile_spheres(c->X, c->N, c->d, c->pos2row, c->mu_f, (float)c->scale, c->tile_w, c->tile_c,
+                                        c->tile_rho, s));
+        const double grow = 1.0 + 0x1p-20;
+        if (is_tensor(c)) {
+            c->lb_R2 = up_f(2.0 * c->margin.R * grow);
+            c->lb_eps = up_f((c->margin.gamma * 4.0 * c->margin.Pmax * c->margin.Pmax + 2.0 * c->margin.Emax) * grow);
+            c->lb_gamma = 0.0f;
+        } else {
+            c->lb_R2 = 0.0f;
+            c->lb_eps = up_f(c->margin.alpha * grow + 1e-37);
+            c->lb_gamma = up_f(c->margin.gamma * grow);
+        }
     }
     c->selc = make_selconst(c->margin);
     return NNM_OK;
@@ -879,6 +939,9 @@ void nnm_destroy(nnm_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     dfree(c->pos2row);
+    dfree(c->tile_c);
+    dfree(c->tile_rho);
+    dfree(c->mu_f);
     dfree(c->row2pos);
     dfree(c->list_pos);
     dfree(c->Xs);
@@ -892,10 +955,15 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->cand_ovf);
     dfree(c->ovf_row);
     dfree(c->ovf_thr);
+    dfree(c->ovf_thr_slot);
+    dfree(c->ovf_flag);
+    dfree(c->ovf_blk);
+    dfree(c->slot_thr);
     dfree(c->coll_cnt);
     dfree(c->coll_j);
     dfree(c->coll_D);
-    dfree(c->heavy_idx);
+    dfree(c->heavy_flag);
+    dfree(c->heavy_blk);
     dfree(c->heavy_rows);
     dfree(c->heavy_rows2);
     dfree(c->heavy_thr);

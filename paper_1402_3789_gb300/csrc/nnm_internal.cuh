@@ -85,7 +85,55 @@ struct SweepArgs {
     int64_t coll_cap;
     // bounded waits of the tensor kernel
     int *err_flag;
+    // tile pruning: bounding spheres of the column tiles (width tile_w positions) over
+    // y = (x - mu_f) * scale_f, and the constants of the lower bound on candidate values
+    int prune;
+    int tile_w;
+    const float *tile_c;      // [ntiles][d]
+    const float *tile_rho;    // [ntiles]
+    const float *mu_f;        // [d] (nullptr: 0)
+    float scale_f;
+    float lb_R2;              // tensor: 2 * max rounding radius (scaled); FP32: 0
+    float lb_eps;             // tensor: max candidate error; FP32: underflow slack
+    float lb_gamma;           // FP32: relative candidate error; tensor: 0
+    const float *X;           // original rows (row-tile spheres)
+    int d;
+    unsigned long long *st_tiles;   // [0] skipped, [1] evaluated column tiles
+    unsigned int *slot_thr;   // [nslots] threshold shared by a row's column ranges (splits > 1)
 };
+
+// Bounding sphere of a set of points y (float, rounded up with a generous slack so that
+// float rounding of y and of the distances can never make a bound invalid).
+__device__ __forceinline__ float sphere_slack(float rho, float ymax)
+{
+    return __fadd_ru(__fmul_ru(rho, 1.0f + 0x1p-12f), __fmul_ru(ymax, 0x1p-12f)) + 1e-30f;
+}
+
+// Lower bound on the candidate value of any pair (row of the sphere (cR, rhoR), column
+// of the sphere (cC, rhoC)): |y_i - y_j| >= |cR - cC| - rhoR - rhoC, the 16-bit operands
+// differ from y by at most R each, and a candidate value differs from the squared
+// operand distance by at most lb_eps (tensor) or a relative lb_gamma (FP32).
+__device__ __forceinline__ float tile_lower_bound(const float *cR, float rhoR, const float *cC, float rhoC, int d,
+                                                  float lb_R2, float lb_eps, float lb_gamma)
+{
+    // fully unrolled so that the (predicated) loads of cC issue together
+    float c[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) c[k] = k < d ? cC[k] : 0.0f;
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (k < d) {
+            const float e = cR[k] - c[k];
+            s = fmaf(e, e, s);
+        }
+    }
+    const float dist = sqrtf(s) * (1.0f - 0x1p-12f);
+    const float gap = dist - rhoR - rhoC - lb_R2;
+    if (!(gap > 0.0f)) return -INFINITY;
+    const float sq = gap * gap * (1.0f - 0x1p-12f);
+    return sq * (1.0f - lb_gamma) - lb_eps;
+}
 
 // Launch the FP32 direct sweep (template on d).
 cudaError_t launch_sweep_fp32(const SweepArgs &a, int d, bool collect, cudaStream_t s);
@@ -114,10 +162,10 @@ struct FinalizeArgs {
     double *res_D;             // [N][k]
     uint8_t *res_n;            // valid results per row (nullable)
     uint8_t *res_exh;          // 1: the results hold every eligible column (nullable)
-    // incomplete rows -> collect pass
-    uint32_t *ovf_cnt;         // single counter
-    uint32_t *ovf_row;         // [nslots] row position of each incomplete slot
-    float *ovf_thr;            // [nslots] its threshold (rounded up)
+    // incomplete rows -> collect pass (compacted afterwards in slot order, so that the
+    // collect pass keeps the spatial order of the rows)
+    uint8_t *ovf_flag;         // [nslots] 1: the slot's candidate lists are incomplete
+    float *ovf_thr;            // [nslots] its threshold (rounded up), where flagged
     // statistics
     unsigned long long *st_max_abs;   // double bits
     unsigned long long *st_max_rel;
@@ -145,8 +193,7 @@ struct CollectRerankArgs {
     uint8_t *res_n;
     uint8_t *res_exh;
     int *retry_flag;           // set when a slot collected more than cap
-    uint32_t *heavy_cnt;       // slots that collected more than cap: count ...
-    uint32_t *heavy_idx;       // ... and their collect-slot indices (+ heavy_base)
+    uint8_t *heavy_flag;       // [heavy_base + p] 1: slot p collected more than cap
     int64_t heavy_base;
     unsigned long long *heavy_max;   // largest such count
     unsigned long long *st_pairs;
@@ -159,13 +206,22 @@ cudaError_t launch_collect_rerank(const CollectRerankArgs &a, cudaStream_t s);
 // Preparation
 // ---------------------------------------------------------------------------------
 cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream_t s);
-// Spatial order: sort keys (landmark group, distance to it, row) for every row.
-cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, nnm_edge *keys, cudaStream_t s);
+// Spatial order: chain rank of the L (<= 1024) landmarks, then sort keys (rank of the
+// row's landmark group, distance to it, row) for every row.
+cudaError_t launch_landmark_chain(const float *X, int64_t N, int d, int64_t L, uint32_t *rank, cudaStream_t s);
+cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, const uint32_t *rank, nnm_edge *keys,
+                                 cudaStream_t s);
 // pos2row[p] = keys[p].a, row2pos[pos2row[p]] = p
 cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,
                                    cudaStream_t s);
 // out[q] = map[in[q]]
 cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *map, int64_t n, uint32_t *out, cudaStream_t s);
+// Ordered compaction: for every q < n with flag[q] != 0, in increasing q, append
+// rows[q] (q itself if rows is null) to out_rows and vals[q] to out_vals; the number
+// appended goes to *count.  block_cnt holds compact_blocks(n) words of scratch.
+int64_t compact_blocks(int64_t n);
+cudaError_t launch_compact(const uint8_t *flag, int64_t n, const uint32_t *rows, const float *vals, uint32_t *block_cnt,
+                           uint32_t *out_rows, float *out_vals, uint32_t *count, cudaStream_t s);
 cudaError_t launch_gather_f32(const uint32_t *in, const float *map, int64_t n, float *out, cudaStream_t s);
 // padded FP32 copy in position order
 cudaError_t launch_pad_fp32(const float *X, int64_t N, int d, int dp, int64_t Npad, const uint32_t *pos2row,
@@ -177,6 +233,9 @@ int mean_blocks(int64_t N);
 cudaError_t launch_max_sqnorm(const float *X, int64_t N, int d, const double *mu,
                               unsigned long long *out_bits, cudaStream_t s);
 // operands written at each row's position; r, P, E stay indexed by original row
+// Bounding spheres of the column tiles (tile_w consecutive positions).
+cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const float *mu_f,
+                                float scale_f, int tile_w, float *tile_c, float *tile_rho, cudaStream_t s);
 cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale,
                                int fp16, int terms, int kpad, int64_t Npad, const uint32_t *row2pos, uint16_t *XA,
                                uint16_t *XB,

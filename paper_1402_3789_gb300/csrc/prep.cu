@@ -35,15 +35,86 @@ cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream
 // Spatial order of the rows.  The sweeps read operands in an order where rows that are
 // close in space are close in memory, so that a row tile meets its near neighbours in
 // its first column tiles and far tiles can be bounded as a whole.  Rows are grouped by
-// their nearest landmark (L rows taken at regular strides), and within a group ordered
-// by their distance to the landmark, then by index: far outliers of a group end up in
-// its last tile.  The order only affects speed: every decision uses original indices
+// their nearest landmark (L rows taken at regular strides), groups follow a nearest-
+// neighbour chain through the landmarks, and within a group rows are ordered by their
+// distance to the landmark, then by index: far outliers of a group end up in its last
+// tile.  The order only affects speed: every decision uses original indices
 // and the exact binary64 distance.
 // ---------------------------------------------------------------------------------
 constexpr int kLandChunk = 128;
+constexpr int kMaxLandmarks = 1024;
+
+// Order of the landmark groups: a greedy nearest-neighbour chain through the landmarks
+// (start at landmark 0, always step to the nearest unvisited one), so that consecutive
+// groups are close in space.  One CTA; landmark m is row m*N/L.
+__global__ void __launch_bounds__(kMaxLandmarks) k_landmark_chain(const float *__restrict__ X, int64_t N, int d,
+                                                                  int L, uint32_t *__restrict__ rank)
+{
+    extern __shared__ float lmk[];   // [L][d]
+    __shared__ float wbest[kMaxLandmarks / 32];
+    __shared__ int warg[kMaxLandmarks / 32];
+    __shared__ int cur_s;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (int q = t; q < L * d; q += blockDim.x) lmk[q] = X[((int64_t)(q / d) * N / L) * d + q % d];
+    bool visited = t >= L;
+    if (t == 0) cur_s = 0;
+    __syncthreads();
+    for (int step = 0; step < L; ++step) {
+        const int cur = cur_s;
+        if (t == cur) {
+            rank[cur] = (uint32_t)step;
+            visited = true;
+        }
+        float v = INFINITY;
+        if (!visited) {
+            float acc = 0.0f;
+            for (int k = 0; k < d; ++k) {
+                const float e = lmk[t * d + k] - lmk[cur * d + k];
+                acc = fmaf(e, e, acc);
+            }
+            v = acc;
+        }
+        int arg = t;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+            const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+            if (ov < v || (ov == v && oa < arg)) {
+                v = ov;
+                arg = oa;
+            }
+        }
+        if (lane == 0) {
+            wbest[w] = v;
+            warg[w] = arg;
+        }
+        __syncthreads();
+        if (t == 0) {
+            float bv = INFINITY;
+            int ba = 0;
+            for (int q = 0; q < (int)(blockDim.x / 32); ++q)
+                if (wbest[q] < bv || (wbest[q] == bv && warg[q] < ba)) {
+                    bv = wbest[q];
+                    ba = warg[q];
+                }
+            cur_s = ba;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_landmark_chain(const float *X, int64_t N, int d, int64_t L, uint32_t *rank, cudaStream_t s)
+{
+    const size_t smem = (size_t)L * d * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_landmark_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_landmark_chain<<<1, kMaxLandmarks, smem, s>>>(X, N, d, (int)L, rank);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 __global__ void __launch_bounds__(256) k_landmark_keys(const float *__restrict__ X, int64_t N, int d, int64_t L,
-                                                       nnm_edge *__restrict__ keys)
+                                                       const uint32_t *__restrict__ rank, nnm_edge *__restrict__ keys)
 {
     __shared__ float lm[kLandChunk * 32];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -78,14 +149,15 @@ __global__ void __launch_bounds__(256) k_landmark_keys(const float *__restrict__
         nnm_edge e;
         e.a = (uint32_t)i;
         e.b = 0u;
-        e.D = (double)arg * 4294967296.0 + (double)__float_as_uint(best);   // exact: < 2^53
+        e.D = (double)rank[arg] * 4294967296.0 + (double)__float_as_uint(best);   // exact: < 2^53
         keys[i] = e;
     }
 }
 
-cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, nnm_edge *keys, cudaStream_t s)
+cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, const uint32_t *rank, nnm_edge *keys,
+                                 cudaStream_t s)
 {
-    k_landmark_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, N, d, L, keys);
+    k_landmark_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, N, d, L, rank, keys);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -123,6 +195,103 @@ cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *map, int64_t n
     return cudaGetLastError();
 }
 
+// Ordered compaction (per-block counts, one prefix over the blocks, ordered scatter).
+constexpr int kCompactThreads = 1024;
+
+int64_t compact_blocks(int64_t n) { return (n + kCompactThreads - 1) / kCompactThreads; }
+
+__global__ void __launch_bounds__(kCompactThreads) k_cmp_count(const uint8_t *__restrict__ flag, int64_t n,
+                                                               uint32_t *__restrict__ block_cnt)
+{
+    const int64_t q = (int64_t)blockIdx.x * kCompactThreads + threadIdx.x;
+    const int c = __syncthreads_count(q < n && flag[q] != 0);
+    if (threadIdx.x == 0) block_cnt[blockIdx.x] = (uint32_t)c;
+}
+
+// exclusive prefix over nb block counts, one block of 1024 threads in chunks of 1024
+__global__ void __launch_bounds__(kCompactThreads) k_cmp_prefix(uint32_t *__restrict__ block_cnt, int64_t nb,
+                                                                uint32_t *__restrict__ count)
+{
+    __shared__ uint32_t ws[kCompactThreads / 32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nb; b0 += kCompactThreads) {
+        const int64_t b = b0 + threadIdx.x;
+        const uint32_t v = b < nb ? block_cnt[b] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) ws[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t t = ws[lane];
+            uint32_t z = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+                if (lane >= o) z += y;
+            }
+            ws[lane] = z - t;
+        }
+        __syncthreads();
+        const uint32_t c0 = carry;
+        if (b < nb) block_cnt[b] = c0 + ws[w] + x - v;
+        __syncthreads();
+        if (threadIdx.x == kCompactThreads - 1) carry = c0 + ws[w] + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_cmp_scatter(const uint8_t *__restrict__ flag, int64_t n,
+                                                                 const uint32_t *__restrict__ rows,
+                                                                 const float *__restrict__ vals,
+                                                                 const uint32_t *__restrict__ block_cnt,
+                                                                 uint32_t *__restrict__ out_rows,
+                                                                 float *__restrict__ out_vals)
+{
+    __shared__ uint32_t ws[kCompactThreads / 32];
+    const int64_t q = (int64_t)blockIdx.x * kCompactThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool f = q < n && flag[q] != 0;
+    const uint32_t bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) ws[w] = __popc(bal);
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t v = ws[lane];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        ws[lane] = x - v;
+    }
+    __syncthreads();
+    if (f) {
+        const uint32_t r = block_cnt[blockIdx.x] + ws[w] + __popc(bal & ((1u << lane) - 1u));
+        out_rows[r] = rows ? rows[q] : (uint32_t)q;
+        if (vals) out_vals[r] = vals[q];
+    }
+}
+
+cudaError_t launch_compact(const uint8_t *flag, int64_t n, const uint32_t *rows, const float *vals, uint32_t *block_cnt,
+                           uint32_t *out_rows, float *out_vals, uint32_t *count, cudaStream_t s)
+{
+    if (n <= 0) return cudaMemsetAsync(count, 0, sizeof(uint32_t), s);
+    const int64_t nb = compact_blocks(n);
+    k_cmp_count<<<(unsigned)nb, kCompactThreads, 0, s>>>(flag, n, block_cnt);
+    k_cmp_prefix<<<1, kCompactThreads, 0, s>>>(block_cnt, nb, count);
+    k_cmp_scatter<<<(unsigned)nb, kCompactThreads, 0, s>>>(flag, n, rows, vals, block_cnt, out_rows, out_vals);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
 __global__ void k_gather_f32(const uint32_t *__restrict__ in, const float *__restrict__ map, int64_t n,
                              float *__restrict__ out)
 {
@@ -134,6 +303,65 @@ cudaError_t launch_gather_f32(const uint32_t *in, const float *map, int64_t n, f
 {
     if (n <= 0) return cudaSuccess;
     k_gather_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, map, n, out);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// One block per column tile: centroid (mean) of y = (x - mu_f) * scale_f over the
+// tile's positions, radius = largest distance to it, enlarged by sphere_slack.
+__global__ void __launch_bounds__(128) k_tile_spheres(const float *__restrict__ X, int64_t N, int d,
+                                                      const uint32_t *__restrict__ pos2row,
+                                                      const float *__restrict__ mu_f, float scale_f, int tile_w,
+                                                      float *__restrict__ tile_c, float *__restrict__ tile_rho)
+{
+    __shared__ float csum[32];
+    __shared__ unsigned int rbits, ybits;
+    __shared__ int cnt;
+    const int64_t p = (int64_t)blockIdx.x * tile_w + threadIdx.x;
+    const bool valid = threadIdx.x < tile_w && p < N;
+    if (threadIdx.x < 32) csum[threadIdx.x] = 0.0f;
+    if (threadIdx.x == 0) {
+        rbits = 0u;
+        ybits = 0u;
+        cnt = 0;
+    }
+    __syncthreads();
+    float y[32];
+    float ny = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        y[k] = 0.0f;
+        if (valid && k < d) {
+            const float x = X[(int64_t)pos2row[p] * d + k];
+            y[k] = (x - (mu_f ? mu_f[k] : 0.0f)) * scale_f;
+            ny = fmaf(y[k], y[k], ny);
+            atomicAdd(&csum[k], y[k]);
+        }
+    }
+    if (valid) {
+        atomicAdd(&cnt, 1);
+        atomicMax(&ybits, __float_as_uint(sqrtf(ny)));
+    }
+    __syncthreads();
+    float dd = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if (k < d) {
+            const float e = y[k] - csum[k] / (float)(cnt > 0 ? cnt : 1);
+            dd = fmaf(e, e, dd);
+        }
+    }
+    if (valid) atomicMax(&rbits, __float_as_uint(sqrtf(dd)));
+    __syncthreads();
+    if (threadIdx.x < d) tile_c[(int64_t)blockIdx.x * d + threadIdx.x] = csum[threadIdx.x] / (float)(cnt > 0 ? cnt : 1);
+    if (threadIdx.x == 0) tile_rho[blockIdx.x] = sphere_slack(__uint_as_float(rbits), __uint_as_float(ybits));
+}
+
+cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const float *mu_f,
+                                float scale_f, int tile_w, float *tile_c, float *tile_rho, cudaStream_t s)
+{
+    const int64_t nt = (N + tile_w - 1) / tile_w;
+    k_tile_spheres<<<(unsigned)nt, 128, 0, s>>>(X, N, d, pos2row, mu_f, scale_f, tile_w, tile_c, tile_rho);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -205,14 +205,12 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
         __syncwarp();
     }
     const double T = threshold(a.m, i, taken < a.k ? INFINITY : (float)vk);
-    if (__any_sync(0xffffffffu, ovf)) {
-        if (lane == 0) {
-            const uint32_t p = atomicAdd(a.ovf_cnt, 1u);
-            a.ovf_row[p] = ipos;
-            a.ovf_thr[p] = __double2float_ru(T);
-        }
-        return;
+    const bool any_ovf = __any_sync(0xffffffffu, ovf);
+    if (lane == 0) {
+        a.ovf_flag[q] = any_ovf ? 1 : 0;
+        if (any_ovf) a.ovf_thr[q] = __double2float_ru(T);
     }
+    if (any_ovf) return;
     const float *xi = a.X + (int64_t)i * a.d;
     for (int e = lane; e < n_ent; e += 32) wD[e] = (wj[e] != kInvalid && (double)wv[e] <= T) ? 0.0 : INFINITY;
     __syncwarp();
@@ -250,12 +248,13 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
     if (p >= a.n) return;
     const uint32_t i = a.pos2row[a.rows[p]];
     const uint32_t cnt = a.coll_cnt[p];
-    if ((int64_t)cnt > a.cap) {
+    const bool heavy = (int64_t)cnt > a.cap;
+    if (lane == 0) a.heavy_flag[a.heavy_base + p] = heavy ? 1 : 0;
+    if (heavy) {
         // too many for this pass's capacity: the count is exact, the host re-runs the
         // row with room for all of them
         if (lane == 0) {
             atomicExch(a.retry_flag, 1);
-            a.heavy_idx[atomicAdd(a.heavy_cnt, 1u)] = (uint32_t)(a.heavy_base + p);
             atomicMax(a.heavy_max, (unsigned long long)cnt);
         }
         return;

@@ -71,12 +71,24 @@ static __device__ __noinline__ int band_push(float v, uint32_t j, int bcnt, int 
     return bcnt + 1;
 }
 
+// Threshold shared by the column ranges (CTAs) of one row: any range's bound T is a
+// valid bound for every range (the final T uses the k-th smallest over all ranges, which
+// is no larger), so each range may prune at the smallest one published.  Stored as the
+// bits of a non-negative float (unsigned order = float order); all ones = none yet.
+__device__ __forceinline__ float shared_thr_exchange(unsigned int *slot_bits, float own)
+{
+    if (own >= 0.0f && own < INFINITY) atomicMin(slot_bits, __float_as_uint(own));
+    const unsigned int g = *reinterpret_cast<volatile unsigned int *>(slot_bits);
+    return g == 0xFFFFFFFFu ? INFINITY : __uint_as_float(g);
+}
+
 template <int KC, int CB>
 struct RowSel {
     static_assert(CB <= kBandMax, "band larger than the output record");
     float tv[KC];
     uint32_t tj[KC];
-    float thr;   // values >= thr (strictly above T) are never needed
+    float thr;   // values above thr are never needed
+    float ext;   // bound learnt from the row's other column ranges
     int bcnt;
     int bovf;
 
@@ -88,8 +100,16 @@ struct RowSel {
             tj[m] = kInvalid;
         }
         thr = valid ? INFINITY : -INFINITY;
+        ext = INFINITY;
         bcnt = 0;
         bovf = 0;
+    }
+
+    // tighten with a bound from another column range of the same row
+    __device__ __forceinline__ void bound(float g)
+    {
+        ext = fminf(ext, g);
+        thr = fminf(thr, ext);
     }
 
     // v <= thr and column j eligible.
@@ -109,7 +129,7 @@ struct RowSel {
                 v = x;
                 j = y;
             }
-            thr = sel_threshold(c, rc, tv[KC - 1]);
+            thr = fminf(sel_threshold(c, rc, tv[KC - 1]), ext);
             if (j != kInvalid && v <= thr) push(v, j, bv, bj, stride);
         } else {
             push(v, j, bv, bj, stride);

@@ -71,7 +71,74 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     // operand rows hold a.dp floats; the tile keeps DP >= a.dp per column (rest zero)
     if (a.dp < DP)
         for (int q = t; q < 2 * kTile * DP; q += kThreads) (&sy[0][0])[q] = 0.0f;
+    // Tile pruning: bounding sphere of this CTA's rows (the operands are the raw rows),
+    // and the block's largest row threshold after each tile.
+    __shared__ float cR[32], wthr[kThreads / 32], blk_thr;
+    __shared__ unsigned int rho_bits, ymax_bits;
+    __shared__ int nvalid;
+    if (t < 32) cR[t] = 0.0f;
+    if (t == 0) {
+        rho_bits = 0u;
+        ymax_bits = 0u;
+        nvalid = 0;
+        blk_thr = INFINITY;
+    }
     __syncthreads();
+    if (a.prune) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!valid[r]) continue;
+            float ny = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                ny = fmaf(x[r][k], x[r][k], ny);
+                atomicAdd(&cR[k], x[r][k]);
+            }
+            atomicAdd(&nvalid, 1);
+            atomicMax(&ymax_bits, __float_as_uint(sqrtf(ny)));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!valid[r]) continue;
+            float dd = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float e = x[r][k] - cR[k] / (float)nvalid;
+                dd = fmaf(e, e, dd);
+            }
+            atomicMax(&rho_bits, __float_as_uint(sqrtf(dd)));
+        }
+        __syncthreads();
+        if (t < D) cR[t] /= (float)(nvalid > 0 ? nvalid : 1);
+    }
+    __syncthreads();
+    const float rhoR = sphere_slack(__uint_as_float(rho_bits), __uint_as_float(ymax_bits));
+    // First kept tile at or after `from`.  Every thread takes the same decision; the lower
+    // bounds of kThreads consecutive tiles are computed together (one per thread) into
+    // lb_s when the scan leaves the current batch.
+    __shared__ float lb_s[kThreads];
+    int64_t lb_base = -(int64_t)kThreads;
+    auto next_kept = [&](int64_t from) -> int64_t {
+        if (!a.prune) return from;
+        const float thr = blk_thr;
+        for (int64_t q = from; q < ntiles; ++q) {
+            if (q >= lb_base + kThreads) {
+                __syncthreads();   // the previous batch is no longer read
+                lb_base = q;
+                float lb = -INFINITY;
+                if (q + t < ntiles) {
+                    const int64_t ct = tile_col(q + t) / kTile;
+                    lb = tile_lower_bound(cR, rhoR, a.tile_c + ct * a.d, a.tile_rho[ct], a.d, 0.0f, a.lb_eps,
+                                          a.lb_gamma);
+                }
+                lb_s[t] = lb;
+                __syncthreads();
+            }
+            if (!(lb_s[q - lb_base] > thr)) return q;
+        }
+        return ntiles;
+    };
     auto load_tile = [&](int64_t tile, int buf) {
         const int64_t j0 = tile_col(tile);
         int64_t n = a.N - j0;
@@ -98,14 +165,41 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
         }
     };
 
-    if (ntiles > 0) load_tile(0, 0);
+    // the block's largest row threshold, for the tile decisions of every thread
+    auto publish = [&](float th0, float th1) {
+        float wt = fmaxf(th0, th1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wt = fmaxf(wt, __shfl_xor_sync(0xffffffffu, wt, o));
+        if ((t & 31) == 0) wthr[t >> 5] = wt;
+        __syncthreads();
+        if (t == 0) {
+            float m = wthr[0];
+            for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, wthr[w]);
+            blk_thr = m;
+        }
+        __syncthreads();
+    };
+    // Thresholds already published for these rows by other column ranges; a collect pass
+    // knows its thresholds from the start.
+    if (!COLLECT && a.splits > 1) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (valid[r]) sel[r].bound(shared_thr_exchange(&a.slot_thr[slot[r]], INFINITY));
+    }
+    if (a.prune) publish(COLLECT ? cthr[0] : sel[0].thr, COLLECT ? cthr[1] : sel[1].thr);
+
+    int64_t tile = next_kept(0);
+    int buf = 0;
+    int64_t swept = 0;
+    if (tile < ntiles) load_tile(tile, 0);
     __pipeline_commit();
-    for (int64_t tile = 0; tile < ntiles; ++tile) {
-        if (tile + 1 < ntiles) load_tile(tile + 1, (int)((tile + 1) & 1));
+    while (tile < ntiles) {
+        const int64_t nxt = next_kept(tile + 1);
+        if (nxt < ntiles) load_tile(nxt, buf ^ 1);
         __pipeline_commit();
         __pipeline_wait_prior(1);
         __syncthreads();
-        const float *ys = sy[tile & 1];
+        const float *ys = sy[buf];
         const int64_t j0 = tile_col(tile);
         const int n = (int)(a.N - j0 < kTile ? a.N - j0 : kTile);
         float th0 = COLLECT ? cthr[0] : sel[0].thr;
@@ -145,7 +239,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
                 th1 = COLLECT ? cthr[1] : sel[1].thr;
             }
         }
-        __syncthreads();
+        if (!COLLECT && a.splits > 1) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                if (valid[r]) sel[r].bound(shared_thr_exchange(&a.slot_thr[slot[r]], sel[r].thr));
+            th0 = sel[0].thr;
+            th1 = sel[1].thr;
+        }
+        if (a.prune) publish(th0, th1);
+        else __syncthreads();
+        tile = nxt;
+        buf ^= 1;
+        ++swept;
+    }
+    if (t == 0 && a.st_tiles) {
+        atomicAdd(&a.st_tiles[0], (unsigned long long)(ntiles - swept));
+        atomicAdd(&a.st_tiles[1], (unsigned long long)swept);
     }
 
     if (!COLLECT) {

@@ -187,12 +187,21 @@ struct __align__(8) TcShared {
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
+    int ring_tile[kMaxStages];   // column tile in each B stage (-1: end of the sequence)
+    int acc_tile[2];             // column tile in each TMEM buffer (-1: end)
+    float warp_thr[kEpiWarps];   // largest row threshold of each epilogue warp
+    float cR[32];                // row tile sphere: centre ...
+    unsigned int rho_bits, ymax_bits;   // ... radius and largest |y| (float bits)
+    int nvalid;
+    int npub;                    // epilogue warps that have published a threshold
 };
+constexpr int kShBytes = 512;
+static_assert(sizeof(TcShared) <= kShBytes, "shared control block");
 
 // Shared-memory stages of the B ring that fit next to the other regions.
 __host__ __device__ inline int tc_stages(int kpad, int band)
 {
-    const size_t fixed = (size_t)kRowTile * kpad * 2 + 256 + (size_t)band * kRowTile * 8 +
+    const size_t fixed = (size_t)kRowTile * kpad * 2 + kShBytes + (size_t)band * kRowTile * 8 +
                          (size_t)kRowTile * kStageStride * 4 + 1024;
     const size_t per = (size_t)kBN * kpad * 2;
     int s = (int)((225 * 1024 - fixed) / per);
@@ -210,7 +219,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     uint8_t *sA = smem_raw;
     uint8_t *sB = smem_raw + a_bytes;
     TcShared *sh = reinterpret_cast<TcShared *>(sB + (size_t)kStages * b_bytes);
-    float *band_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(sh) + 256);   // [CB][256]
+    float *band_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(sh) + kShBytes);   // [CB][256]
     uint32_t *band_j = reinterpret_cast<uint32_t *>(band_v + CB * kRowTile);
     float *stage_v = reinterpret_cast<float *>(band_j + CB * kRowTile);                  // [256][kStageStride]
 
@@ -234,11 +243,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             mbar_init(&sh->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&sh->tfull[b], 1);
+            mbar_init(&sh->tfull[b], 2);   // the MMA completion and the tile number
             mbar_init(&sh->tempty[b], kEpiWarps);
         }
         mbar_init(&sh->drain, 1);
         sh->abort_flag = 0;
+        for (int w = 0; w < kEpiWarps; ++w) sh->warp_thr[w] = INFINITY;
+        for (int k = 0; k < 32; ++k) sh->cR[k] = 0.0f;
+        sh->rho_bits = 0u;
+        sh->ymax_bits = 0u;
+        sh->nvalid = 0;
+        sh->npub = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
@@ -248,10 +263,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
 
+    __syncthreads();
     // Row operand tile: 256 rows gathered (a row list, or consecutive rows) into the
-    // interleaved layout by the epilogue threads.
+    // interleaved layout by the epilogue threads; with pruning, also the bounding sphere
+    // of the tile's rows (centre = mean of y, radius = largest distance to it).
     int myrow_slot = -1;
     uint32_t myrow = 0, mycomp = 0;
+    float yv[32];
     if (warp < kEpiWarps) {
         const int r = (warp >> 2) * 128 + (warp & 3) * 32 + lane;   // row within the tile
         const int64_t slot = slot0 + r;
@@ -268,38 +286,119 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             for (int c = 0; c < chunks; ++c) dst[((r >> 3) * chunks + c) * 8 + (r & 7)] = make_uint4(0, 0, 0, 0);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (a.prune && myrow_slot >= 0) {
+            const float *xr = a.X + (int64_t)a.pos2row[myrow] * a.d;
+            float ny = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                yv[k] = 0.0f;
+                if (k < a.d) {
+                    yv[k] = (xr[k] - (a.mu_f ? a.mu_f[k] : 0.0f)) * a.scale_f;
+                    ny = fmaf(yv[k], yv[k], ny);
+                    atomicAdd(&sh->cR[k], yv[k]);
+                }
+            }
+            atomicAdd(&sh->nvalid, 1);
+            atomicMax(&sh->ymax_bits, __float_as_uint(sqrtf(ny)));
+        }
+    }
+    __syncthreads();
+    if (a.prune && warp < kEpiWarps && myrow_slot >= 0) {
+        float dd = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < a.d) {
+                const float e = yv[k] - sh->cR[k] / (float)sh->nvalid;
+                dd = fmaf(e, e, dd);
+            }
+        atomicMax(&sh->rho_bits, __float_as_uint(sqrtf(dd)));
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (a.prune && threadIdx.x < 32 && threadIdx.x < a.d) sh->cR[threadIdx.x] /= (float)(sh->nvalid > 0 ? sh->nvalid : 1);
+    __syncthreads();
     const uint32_t tmem = sh->tmem_base;
     volatile int *abort_flag = &sh->abort_flag;
 
     if (warp == kProdWarp) {
-        // whole warp walks the loop; lane 0 waits and issues, the result is broadcast
-        int issued = 0;
-        for (int t = 0; t < ntiles; ++t) {
-            const int s = t % kStages;
+        // Whole warp walks the column tiles; lane 0 decides, waits and issues.  A tile is
+        // skipped when the lower bound of its candidate values exceeds every row's
+        // threshold (the epilogue's published maxima, possibly stale = larger = safe).
+        // The kept tiles' numbers travel with the stages; -1 ends the sequence.
+        const float rhoR = sphere_slack(__uint_as_float(sh->rho_bits), __uint_as_float(sh->ymax_bits));
+        int issued = 0, skipped = 0;
+        bool stop = false;
+        // lower bounds of 32 consecutive tiles at a time, one per lane (they do not depend
+        // on the thresholds, which are read fresh at each decision)
+        int lb_base = -32;
+        float lb_lane = -INFINITY;
+        for (int t = 0; t <= ntiles && !stop; ++t) {
+            const bool last = t == ntiles;
+            const int64_t col = last ? -1 : tile_col(t);
+            int keep = 1;
+            if (!last && a.prune) {
+                if (t >= lb_base + 32) {
+                    lb_base = t;
+                    lb_lane = -INFINITY;
+                    if (t + lane < ntiles) {
+                        const int64_t ct = tile_col(t + lane) / kBN;
+                        lb_lane = tile_lower_bound(sh->cR, rhoR, a.tile_c + ct * a.d, a.tile_rho[ct], a.d, a.lb_R2,
+                                                   a.lb_eps, a.lb_gamma);
+                    }
+                }
+                const float lb = __shfl_sync(0xffffffffu, lb_lane, t - lb_base);
+                if (lane == 0) {
+                    float thr = -INFINITY;
+                    for (int w = 0; w < kEpiWarps; ++w) thr = fmaxf(thr, ((volatile float *)sh->warp_thr)[w]);
+                    keep = !(lb > thr);
+                }
+            }
+            keep = __shfl_sync(0xffffffffu, keep, 0);
+            if (a.prune && t == 1 && lane == 0) {
+                // Every later decision waits for the thresholds the epilogue learns from the
+                // first tile (the nearest columns), not for the initial "none yet": one tile
+                // of pipeline fill per CTA.  Bounded; on time-out the decisions only get
+                // less selective.
+                const uint64_t t0 = global_ns();
+                while (((volatile int *)&sh->npub)[0] < kEpiWarps && !*abort_flag && global_ns() - t0 < kWaitNs)
+                    __nanosleep(64);
+            }
+            if (!keep) {
+                ++skipped;
+                continue;
+            }
+            const int s = issued % kStages;
             int ok = 1;
-            if (lane == 0 && t >= kStages) ok = mbar_wait(&sh->empty[s], ((t / kStages) - 1) & 1, abort_flag);
+            if (lane == 0 && issued >= kStages)
+                ok = mbar_wait(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 *abort_flag = 1;
                 break;
             }
             if (lane == 0) {
-                mbar_arrive_expect_tx(&sh->full[s], b_bytes);
-                const int64_t col = tile_col(t);
-                bulk_g2s(sB + (size_t)s * b_bytes, a.XB + col * kpad, b_bytes, &sh->full[s]);
+                sh->ring_tile[s] = last ? -1 : (int)(col / kBN);
+                if (last) {
+                    mbar_arrive(&sh->full[s]);
+                } else {
+                    mbar_arrive_expect_tx(&sh->full[s], b_bytes);
+                    bulk_g2s(sB + (size_t)s * b_bytes, a.XB + col * kpad, b_bytes, &sh->full[s]);
+                }
             }
-            issued = t + 1;
+            ++issued;
+            stop = last;
             __syncwarp();
+        }
+        if (lane == 0 && a.st_tiles) {
+            atomicAdd(&a.st_tiles[0], (unsigned long long)skipped);
+            atomicAdd(&a.st_tiles[1], (unsigned long long)(issued > 0 ? issued - 1 : 0));
         }
         // drain: every issued copy must have landed before the CTA exits
         if (lane == 0) {
-            for (int t = issued - kStages < 0 ? 0 : issued - kStages; t < issued; ++t) {
+            for (int q = issued - kStages < 0 ? 0 : issued - kStages; q < issued; ++q) {
                 const uint64_t t0 = global_ns();
-                while (!mbar_try_wait(&sh->full[t % kStages], (t / kStages) & 1) && global_ns() - t0 < kWaitNs)
+                while (!mbar_try_wait(&sh->full[q % kStages], (q / kStages) & 1) && global_ns() - t0 < kWaitNs)
                     __nanosleep(256);
             }
         }
@@ -310,34 +409,46 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB);
         const int ksteps = kpad / 16;
         int done = 0;
-        for (int t = 0; t < ntiles; ++t) {
-            const int s = t % kStages, b = t & 1;
+        for (int q = 0;; ++q) {
+            const int s = q % kStages, b = q & 1;
             int ok = 1;
             if (lane == 0) {
-                ok = mbar_wait(&sh->full[s], (t / kStages) & 1, abort_flag);
-                if (ok && t >= 2) ok = mbar_wait(&sh->tempty[b], ((t >> 1) - 1) & 1, abort_flag);
+                ok = mbar_wait(&sh->full[s], (q / kStages) & 1, abort_flag);
+                if (ok && q >= 2) ok = mbar_wait(&sh->tempty[b], ((q >> 1) - 1) & 1, abort_flag);
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 *abort_flag = 1;
                 break;
             }
+            // lane 0 observed the stage (acquire); it reads the tile number and the warp
+            // takes its decision from lane 0 so that all lanes stay together
+            int tile = 0;
+            if (lane == 0) tile = ((volatile int *)sh->ring_tile)[s];
+            tile = __shfl_sync(0xffffffffu, tile, 0);
             tc_fence_after();
             if (lane == 0) {
+                ((volatile int *)sh->acc_tile)[b] = tile;
+                if (tile >= 0) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t d_tmem = tmem + (uint32_t)((b * 2 + h) * kBN);
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        uint64_t ad = smem_desc(aaddr + (uint32_t)h * 16u * sbo + (uint32_t)kk * 256u, lbo, sbo);
-                        uint64_t bd = smem_desc(baddr + (uint32_t)s * b_bytes + (uint32_t)kk * 256u, lbo, sbo);
-                        mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t d_tmem = tmem + (uint32_t)((b * 2 + h) * kBN);
+                        for (int kk = 0; kk < ksteps; ++kk) {
+                            uint64_t ad = smem_desc(aaddr + (uint32_t)h * 16u * sbo + (uint32_t)kk * 256u, lbo, sbo);
+                            uint64_t bd = smem_desc(baddr + (uint32_t)s * b_bytes + (uint32_t)kk * 256u, lbo, sbo);
+                            mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        }
                     }
+                    mma_commit(&sh->empty[s]);
+                    mma_commit(&sh->tfull[b]);
+                } else {
+                    mbar_arrive(&sh->tfull[b]);   // no MMA for the end marker
                 }
-                mma_commit(&sh->empty[s]);
-                mma_commit(&sh->tfull[b]);
+                mbar_arrive(&sh->tfull[b]);       // publishes acc_tile[b]
             }
-            done = t + 1;
             __syncwarp();
+            if (tile < 0) break;
+            done = q + 1;
         }
         // every issued MMA completes before TMEM is freed
         if (lane == 0 && done > 0) {
@@ -358,6 +469,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         uint32_t *bj = band_j + threadIdx.x;
         float *stg = stage_v + threadIdx.x * kStageStride;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
+        // Thresholds already published for these rows by other column ranges, then the
+        // warp's first publication (a collect pass knows its thresholds from the start).
+        if (!COLLECT && a.splits > 1 && valid) sel.bound(shared_thr_exchange(&a.slot_thr[slot0 + myrow_slot], INFINITY));
+        auto publish = [&]() {
+            float wt = COLLECT ? cthr : sel.thr;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wt = fmaxf(wt, __shfl_xor_sync(0xffffffffu, wt, o));
+            if (lane == 0) ((volatile float *)sh->warp_thr)[warp] = wt;
+        };
+        bool published = false;
+        if (a.prune && COLLECT) {
+            publish();
+            __syncwarp();
+            if (lane == 0) atomicAdd(&sh->npub, 1);
+            published = true;
+        }
         // Fast test of 32 values against the row's threshold: a 3-input integer min over the
         // FP32 bit patterns.  For non-negative values the integer order is the float order;
         // a negative value compares below every non-negative threshold, so it can only raise
@@ -398,17 +525,25 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 }
             }
         };
-        for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1;
+        for (int q = 0;; ++q) {
+            const int b = q & 1;
             int ok = 1;
-            if (lane == 0) ok = mbar_wait(&sh->tfull[b], (t >> 1) & 1, abort_flag);
+            if (lane == 0) ok = mbar_wait(&sh->tfull[b], (q >> 1) & 1, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 *abort_flag = 1;
                 break;
             }
+            // every lane acquires the completed phase itself before reading TMEM (the phase
+            // cannot move on before this warp releases the buffer, so this returns at once);
+            // the tile number comes from lane 0 so that the whole warp decides alike
+            mbar_try_wait(&sh->tfull[b], (q >> 1) & 1);
             tc_fence_after();
-            const int64_t col0 = tile_col(t);
+            int tile = 0;
+            if (lane == 0) tile = ((volatile int *)sh->acc_tile)[b];
+            tile = __shfl_sync(0xffffffffu, tile, 0);
+            if (tile < 0) break;
+            const int64_t col0 = (int64_t)tile * kBN;
             const uint32_t taddr = lane_base + (uint32_t)((b * 2 + half) * kBN);
 #pragma unroll 1
             for (int hh = 0; hh < kBN / 64; ++hh) {
@@ -431,6 +566,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 }
                 __syncwarp();
             }
+            if (!COLLECT && a.splits > 1 && valid)
+                sel.bound(shared_thr_exchange(&a.slot_thr[slot0 + myrow_slot], sel.thr));
+            if (a.prune) {
+                publish();
+                if (!published) {
+                    __syncwarp();
+                    if (lane == 0) atomicAdd(&sh->npub, 1);
+                    published = true;
+                }
+            }
         }
         if (!COLLECT && valid) {
             const int64_t rec = (slot0 + myrow_slot) * a.splits + split;
@@ -452,7 +597,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
 size_t sweep_tc_smem_bytes(int kpad, int band)
 {
     // at least ~half of the SM's shared memory keeps one CTA per SM (it holds all of TMEM)
-    const size_t need = (size_t)kRowTile * kpad * 2 + (size_t)tc_stages(kpad, band) * kBN * kpad * 2 + 256 +
+    const size_t need = (size_t)kRowTile * kpad * 2 + (size_t)tc_stages(kpad, band) * kBN * kpad * 2 + kShBytes +
                         (size_t)band * kRowTile * 8 + (size_t)kRowTile * kStageStride * 4 + 1024;
     const size_t one_per_sm = 120 * 1024;
     return need > one_per_sm ? need : one_per_sm;

@@ -38,7 +38,7 @@ class NNMError(RuntimeError):
 
 class nnm_options(ctypes.Structure):
     _fields_ = [("cache_k", ctypes.c_int32), ("freeze_at_cap", ctypes.c_int32),
-                ("col_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("col_split", ctypes.c_int32), ("no_tile_pruning", ctypes.c_int32)]
 
 
 class nnm_restrictions(ctypes.Structure):
@@ -56,7 +56,8 @@ class nnm_stats(ctypes.Structure):
                [("max_abs_err", ctypes.c_double), ("max_rel_err", ctypes.c_double),
                 ("sweep_ms_per_launch_full", ctypes.c_double), ("full_sweep_pairs", ctypes.c_int64),
                 ("k_pad", ctypes.c_int32), ("cache_k", ctypes.c_int32), ("scale", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("tiles_skipped", ctypes.c_int64),
+                ("tiles_swept", ctypes.c_int64)]
 
 
 # every symbol include/nnm.h declares
@@ -132,14 +133,15 @@ class Context:
 
 
 def nnm_create(X: torch.Tensor, precision: str = "fp32", stream: torch.cuda.Stream | None = None,
-               cache_k: int = 0, freeze_at_cap: bool = False, col_split: int = 0) -> Context:
+               cache_k: int = 0, freeze_at_cap: bool = False, col_split: int = 0,
+               tile_pruning: bool = True) -> Context:
     """nnm_create: X is a contiguous float32 [N, d] CUDA tensor (kept alive by the context)."""
     lib = load_library()
     if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
         raise ValueError("X must be a float32 [N, d] CUDA tensor")
     X = X.contiguous()
     stream = stream or torch.cuda.current_stream(X.device)
-    opt = nnm_options(int(cache_k), int(bool(freeze_at_cap)), int(col_split), 0)
+    opt = nnm_options(int(cache_k), int(bool(freeze_at_cap)), int(col_split), int(not tile_pruning))
     h = ctypes.c_void_p()
     st = lib.nnm_create(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], 0, PRECISIONS[precision],
                         ctypes.c_void_p(stream.cuda_stream), ctypes.byref(opt), ctypes.byref(h))

@@ -255,3 +255,22 @@ def test_candidates_are_tight(nnm, precision):
     assert st["rerank_pairs"] <= 12 * 4096
     bound = {"fp32": 10 * 2.0 ** -24, "fp16": 0.05, "bf16": 0.25, "bf16x3": 0.01}[precision]
     assert st["max_rel_err"] <= bound
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_tile_pruning_skips_far_tiles_and_changes_nothing(nnm, orc, precision):
+    # Well separated blobs: the bounding-sphere bound must skip most column tiles,
+    # and the exact results must equal both the unpruned run and the oracle.
+    rng = np.random.default_rng(17)
+    centres = rng.uniform(0, 400, (24, 6))
+    X = (centres[rng.integers(0, 24, 9000)] + rng.standard_normal((9000, 6))).astype(np.float32)
+    idx_p, D_p, st_p = run_nearest(nnm, X, 4, precision)
+    idx_u, D_u, st_u = run_nearest(nnm, X, 4, precision, tile_pruning=False)
+    oi, oD = orc.knn(X, 4)
+    assert np.array_equal(idx_p, oi) and np.array_equal(D_p, oD)
+    assert np.array_equal(idx_u, oi) and np.array_equal(D_u, oD)
+    assert st_u["tiles_skipped"] == 0
+    assert st_p["tiles_skipped"] > 0.3 * (st_p["tiles_skipped"] + st_p["tiles_swept"])
+    tree_p, m_p, lab_p, K_p, _ = run_cluster(nnm, X, {"max_join_dist": 3.0}, precision)
+    otree, om, olab, oK = orc.cluster(X, {"max_join_dist": 3.0})
+    assert np.array_equal(tree_p, otree) and np.array_equal(m_p, om) and np.array_equal(lab_p, olab)
