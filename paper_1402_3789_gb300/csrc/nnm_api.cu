@@ -12,6 +12,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -76,6 +77,8 @@ struct nnm_ctx {
     uint32_t *cache_j = nullptr;
     double *cache_D = nullptr;
     uint8_t *cache_n = nullptr, *cache_exh = nullptr;
+    double *row_B = nullptr;
+    unsigned long long *comp_bound = nullptr;
     uint32_t *comp = nullptr, *parent = nullptr, *list = nullptr;
     unsigned long long *row_D = nullptr, *row_ab = nullptr, *best_D = nullptr, *best_ab = nullptr;
     uint8_t *row_state = nullptr, *frozen = nullptr, *flag_pos = nullptr;
@@ -323,7 +326,8 @@ constexpr size_t kCollectBytes = (size_t)4 << 30;   // collect buffers (uint32 +
 // columns per row; rows that collected more are gathered and run again with room for
 // their exact count.
 nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n, int64_t cap, int k,
-                   const uint32_t *comp, uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh)
+                   const uint32_t *comp, uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh,
+                   const double *row_B)
 {
     cudaStream_t s = c->stream;
     NNM_TRY(ensure_heavy(c, (size_t)n));
@@ -373,6 +377,7 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
             ra.res_D = res_D;
             ra.res_n = res_n;
             ra.res_exh = res_exh;
+            ra.row_B = row_B;
             ra.retry_flag = &c->derr[1];
             ra.heavy_flag = c->heavy_flag;
             ra.heavy_base = b0;
@@ -406,7 +411,8 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
 // Eligible: j != i, and comp[j] != comp[i] if comp is given.  Results go to
 // res_j/res_D [row][k] (and res_n / res_exh if given).
 nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, const uint32_t *comp,
-                   uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh, bool full)
+                   uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh, bool full,
+                   const double *row_B = nullptr)
 {
     if (nslots <= 0) return NNM_OK;
     const int S = choose_splits(c, nslots);
@@ -425,6 +431,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     sa.out_j = c->cand_j;
     sa.out_ovf = c->cand_ovf;
     sa.kc = k;
+    sa.row_B = row_B;
     sa.slot_thr = c->slot_thr;
     if (splits > 1) NNM_CUDA(c, cudaMemsetAsync(c->slot_thr, 0xFF, (size_t)nslots * sizeof(unsigned int), c->stream));
     {
@@ -461,6 +468,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
         fa.res_D = res_D;
         fa.res_n = res_n;
         fa.res_exh = res_exh;
+        fa.row_B = row_B;
         fa.ovf_flag = c->ovf_flag;
         fa.ovf_thr = c->ovf_thr_slot;
         fa.st_max_abs = &c->dstat[0];
@@ -480,7 +488,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     // run again with room for all of them.  Batches keep the buffers within kCollectBytes.
     c->stats.rows_overflowed += novf;
     NNM_TRY(collect(c, c->ovf_row, c->ovf_thr, novf, is_tensor(c) ? 1024 : 256, k, comp, res_j, res_D, res_n,
-                    res_exh));
+                    res_exh, row_B));
     return NNM_OK;
 }
 
@@ -536,27 +544,71 @@ nnm_status prepare(nnm_ctx *c)
     NNM_CUDA(c, cudaStreamSynchronize(s));
     if (bad) return fail(c, NNM_ENONFINITE, "X holds NaN or infinite values");
 
-    // spatial order: landmark groups, sorted by (group, distance to the landmark, row)
+    // spatial order: landmark groups along a chain of coarse landmarks, isolated rows last
     {
         NNM_TRY(dalloc(c, &c->pos2row, (size_t)c->N));
         NNM_TRY(dalloc(c, &c->row2pos, (size_t)c->N));
         NNM_TRY(dalloc(c, &c->list_pos, (size_t)c->N));
-        nnm_edge *keys = nullptr, *tmp = nullptr, *sorted = nullptr;
-        NNM_TRY(dalloc(c, &keys, (size_t)c->N));
-        NNM_TRY(dalloc(c, &tmp, (size_t)c->N));
-        int64_t L = c->N / 256;
-        if (L > 1024) L = 1024;
+        int64_t L = c->N / 512;
+        if (L > kMaxGroups) L = kMaxGroups;
         if (L < 1) L = 1;
-        uint32_t *rank = nullptr;
-        NNM_TRY(dalloc(c, &rank, (size_t)L));
-        NNM_CUDA(c, launch_landmark_chain(c->X, c->N, c->d, L, rank, s));
-        NNM_CUDA(c, launch_landmark_keys(c->X, c->N, c->d, L, rank, keys, s));
-        NNM_CUDA(c, launch_sort_edges(keys, tmp, c->N, s, &sorted));
-        NNM_CUDA(c, launch_order_from_keys(sorted, c->N, c->pos2row, c->row2pos, s));
-        NNM_CUDA(c, cudaStreamSynchronize(s));
-        cudaFree(keys);
-        cudaFree(tmp);
-        cudaFree(rank);
+        const int64_t S = L < 1024 ? L : 1024;
+        nnm_edge *keys = nullptr, *tmp = nullptr, *sorted = nullptr, *lkeys = nullptr, *ltmp = nullptr,
+                 *lsorted = nullptr;
+        uint32_t *crank = nullptr, *larg = nullptr, *lpos = nullptr, *lrank = nullptr, *rarg = nullptr;
+        float *ldist = nullptr, *rdist = nullptr, *tau = nullptr;
+        unsigned int *hist = nullptr;
+        auto free_all = [&]() {
+            cudaFree(keys);
+            cudaFree(tmp);
+            cudaFree(lkeys);
+            cudaFree(ltmp);
+            cudaFree(crank);
+            cudaFree(larg);
+            cudaFree(lpos);
+            cudaFree(lrank);
+            cudaFree(rarg);
+            cudaFree(ldist);
+            cudaFree(rdist);
+            cudaFree(tau);
+            cudaFree(hist);
+        };
+        nnm_status st = NNM_OK;
+        do {
+            if ((st = dalloc(c, &keys, (size_t)c->N)) != NNM_OK) break;
+            if ((st = dalloc(c, &tmp, (size_t)c->N)) != NNM_OK) break;
+            if ((st = dalloc(c, &lkeys, (size_t)L)) != NNM_OK) break;
+            if ((st = dalloc(c, &ltmp, (size_t)L)) != NNM_OK) break;
+            if ((st = dalloc(c, &crank, (size_t)S)) != NNM_OK) break;
+            if ((st = dalloc(c, &larg, (size_t)L)) != NNM_OK) break;
+            if ((st = dalloc(c, &lpos, (size_t)L)) != NNM_OK) break;
+            if ((st = dalloc(c, &lrank, (size_t)L)) != NNM_OK) break;
+            if ((st = dalloc(c, &ldist, (size_t)L)) != NNM_OK) break;
+            if ((st = dalloc(c, &rarg, (size_t)c->N)) != NNM_OK) break;
+            if ((st = dalloc(c, &rdist, (size_t)c->N)) != NNM_OK) break;
+            if ((st = dalloc(c, &tau, 1)) != NNM_OK) break;
+            if ((st = dalloc(c, &hist, 4096)) != NNM_OK) break;
+        } while (0);
+        if (st != NNM_OK) {
+            free_all();
+            return st;
+        }
+        cudaError_t e = launch_landmark_chain(c->X, c->N, c->d, S, crank, s);
+        if (e == cudaSuccess) e = launch_nearest_ref(c->X, c->N, c->d, L, S, larg, ldist, s);
+        if (e == cudaSuccess)
+            e = launch_spatial_keys(larg, ldist, L, crank, nullptr, nullptr, 0, nullptr, nullptr, nullptr, lkeys,
+                                    nullptr, 0, s);
+        if (e == cudaSuccess) e = launch_sort_edges(lkeys, ltmp, L, s, &lsorted);
+        if (e == cudaSuccess) e = launch_order_from_keys(lsorted, L, lpos, lrank, s);
+        if (e == cudaSuccess) e = launch_nearest_ref(c->X, c->N, c->d, c->N, L, rarg, rdist, s);
+        if (e == cudaSuccess)
+            e = launch_spatial_keys(nullptr, nullptr, 0, nullptr, rarg, rdist, c->N, lrank, hist, tau, nullptr, keys, 1,
+                                    s);
+        if (e == cudaSuccess) e = launch_sort_edges(keys, tmp, c->N, s, &sorted);
+        if (e == cudaSuccess) e = launch_order_from_keys(sorted, c->N, c->pos2row, c->row2pos, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        free_all();
+        if (e != cudaSuccess) return fail(c, NNM_ECUDA, "spatial order: %s", cudaGetErrorString(e));
     }
     if (!is_tensor(c)) {
         c->dp = (c->d + 3) & ~3;
@@ -658,6 +710,8 @@ nnm_status ensure_rounds(nnm_ctx *c)
     NNM_TRY(dalloc(c, &c->cache_D, (size_t)N * c->kc));
     NNM_TRY(dalloc(c, &c->cache_n, (size_t)N));
     NNM_TRY(dalloc(c, &c->cache_exh, (size_t)N));
+    NNM_TRY(dalloc(c, &c->row_B, (size_t)N));
+    NNM_TRY(dalloc(c, &c->comp_bound, (size_t)N));
     NNM_TRY(dalloc(c, &c->parent, (size_t)N));
     NNM_TRY(dalloc(c, &c->list, (size_t)N));
     NNM_TRY(dalloc(c, &c->row_D, (size_t)N));
@@ -705,6 +759,10 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     st.cache_D = c->cache_D;
     st.cache_n = c->cache_n;
     st.cache_exh = c->cache_exh;
+    st.row_B = c->row_B;
+    st.comp_bound = c->comp_bound;
+    st.X = c->X;
+    st.d = c->d;
     st.row_D = c->row_D;
     st.row_ab = c->row_ab;
     st.row_state = c->row_state;
@@ -727,7 +785,23 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
         NNM_CUDA(c, cudaMemsetAsync(&c->dcount[1], 0, 4 * sizeof(uint32_t), s));
     }
     int64_t ncomp = c->N;
+    // NNM_TRACE=1 in the environment: one line per merge round on stderr
+    const char *trace_env = getenv("NNM_TRACE");
+    const bool trace = trace_env && trace_env[0] == '1';
+    auto tiles_now = [&](unsigned long long *t) {
+        cudaMemcpyAsync(t, &c->dstat[13], 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+    };
+    if (trace) {
+        unsigned long long t[2];
+        tiles_now(t);
+        fprintf(stderr, "nnm initial k=%d: sweep %.2f ms, rerank %.2f ms, tiles swept %llu skipped %llu, overflowed %lld\n",
+                c->kc, c->stats.ms_sweep, c->stats.ms_rerank, t[1], t[0], (long long)c->stats.rows_overflowed);
+    }
     for (int round = 0; ncomp > 1; ++round) {
+        const double sweep0 = c->stats.ms_sweep, rerank0 = c->stats.ms_rerank;
+        unsigned long long t0[2] = {0, 0}, t1[2] = {0, 0};
+        if (trace) tiles_now(t0);
         if (round > 64) return fail(c, NNM_ECUDA, "merge rounds did not converge");
         c->stats.rounds = round + 1;
         uint32_t nres = 0;
@@ -741,7 +815,7 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
         if (nres > 0) {
             c->stats.rows_rescanned += nres;
             NNM_TRY(run_knn(c, c->list_pos, nres, c->kc, c->comp, c->cache_j, c->cache_D, c->cache_n, c->cache_exh,
-                            false));
+                            false, c->row_B));
             Phase ph(c, &c->stats.ms_rounds);
             NNM_CUDA(c, launch_resolve(st, c->list, nres, s));
             NNM_CUDA(c, launch_component_min(st, s));
@@ -767,6 +841,13 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
             NNM_CUDA(c, launch_relabel(st, s));
         }
         ncomp -= nedge;
+        if (trace) {
+            tiles_now(t1);
+            fprintf(stderr, "nnm round %d: rescans %u, sweep %.2f ms, rerank %.2f ms, tiles swept %llu skipped %llu, "
+                            "edges %u, components %lld\n",
+                    round, nres, c->stats.ms_sweep - sweep0, c->stats.ms_rerank - rerank0, t1[1] - t0[1],
+                    t1[0] - t0[0], nedge, (long long)ncomp);
+        }
     }
     uint32_t ne = 0;
     NNM_TRY(read_dev(c, &ne, &c->dcount[4]));
@@ -972,6 +1053,8 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->cache_D);
     dfree(c->cache_n);
     dfree(c->cache_exh);
+    dfree(c->row_B);
+    dfree(c->comp_bound);
     dfree(c->comp);
     dfree(c->parent);
     dfree(c->list);

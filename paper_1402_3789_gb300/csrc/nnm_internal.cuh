@@ -22,6 +22,19 @@ constexpr int kRowTile = 256;     // rows per sweep CTA (both candidate paths)
 constexpr int kMaxSplits = 32;    // column ranges per row tile
 constexpr uint64_t kMaxKey = 0xFFFFFFFFFFFFFFFFull;
 
+// The exact squared distance of Eq. (1): D = ((t_0 + t_1) + ...) + t_{d-1},
+// t_k = e_k * e_k, e_k = x_ik - x_jk, each operation binary64 round-to-nearest, no
+// contraction (the same value for (i, j) and (j, i)).
+__device__ __forceinline__ double canon_D(const float *__restrict__ xi, const float *__restrict__ xj, int d)
+{
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) {
+        const double e = __dsub_rn((double)xi[k], (double)xj[k]);
+        s = __dadd_rn(s, __dmul_rn(e, e));
+    }
+    return s;
+}
+
 struct Margin {
     int tensor;         // 0: FP32 direct candidates; 1: tensor-core candidates
     double gamma;       // relative error bound of one candidate value
@@ -64,6 +77,9 @@ struct SweepArgs {
     // rows and columns are positions in the spatial order of the operands
     const uint32_t *rows;     // slot -> row position (nullptr: slot q is position q)
     int64_t nslots;
+    const double *row_B;      // per original row: only columns with exact D <= row_B are
+                              // wanted (nullptr: no bound); a bound lowers the starting
+                              // threshold of the row
     const uint32_t *pos2row;  // position -> original row index
     // eligibility
     const uint32_t *comp;     // nullptr: every column j != i is eligible; else comp[row(j)] != comp[row(i)]
@@ -162,6 +178,7 @@ struct FinalizeArgs {
     double *res_D;             // [N][k]
     uint8_t *res_n;            // valid results per row (nullable)
     uint8_t *res_exh;          // 1: the results hold every eligible column (nullable)
+    const double *row_B;       // per original row: keep only D <= row_B (nullptr: no bound)
     // incomplete rows -> collect pass (compacted afterwards in slot order, so that the
     // collect pass keeps the spatial order of the rows)
     uint8_t *ovf_flag;         // [nslots] 1: the slot's candidate lists are incomplete
@@ -192,6 +209,7 @@ struct CollectRerankArgs {
     double *res_D;
     uint8_t *res_n;
     uint8_t *res_exh;
+    const double *row_B;       // as in FinalizeArgs
     int *retry_flag;           // set when a slot collected more than cap
     uint8_t *heavy_flag;       // [heavy_base + p] 1: slot p collected more than cap
     int64_t heavy_base;
@@ -206,12 +224,18 @@ cudaError_t launch_collect_rerank(const CollectRerankArgs &a, cudaStream_t s);
 // Preparation
 // ---------------------------------------------------------------------------------
 cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream_t s);
-// Spatial order: chain rank of the L (<= 1024) landmarks, then sort keys (rank of the
-// row's landmark group, distance to it, row) for every row.
+// Spatial order (prep.cu): chain rank of S <= 1024 coarse landmarks; nearest reference
+// row of each query row (queries and references at regular strides of X); sort keys of
+// the landmarks (which = 0) or of the rows (which = 1, with the isolation threshold from
+// a histogram of 4096 bins); positions from sorted keys.
+constexpr int kMaxGroups = 4096;
 cudaError_t launch_landmark_chain(const float *X, int64_t N, int d, int64_t L, uint32_t *rank, cudaStream_t s);
-cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, const uint32_t *rank, nnm_edge *keys,
-                                 cudaStream_t s);
-// pos2row[p] = keys[p].a, row2pos[pos2row[p]] = p
+cudaError_t launch_nearest_ref(const float *X, int64_t N, int d, int64_t Q, int64_t R, uint32_t *arg, float *dist,
+                               cudaStream_t s);
+cudaError_t launch_spatial_keys(const uint32_t *larg, const float *ldist, int64_t L, const uint32_t *crank,
+                                const uint32_t *rarg, const float *rdist, int64_t N, const uint32_t *lrank,
+                                unsigned int *hist, float *tau, nnm_edge *lkeys, nnm_edge *rkeys, int which,
+                                cudaStream_t s);
 cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,
                                    cudaStream_t s);
 // out[q] = map[in[q]]
@@ -254,6 +278,12 @@ struct RoundState {
     const double *cache_D;
     const uint8_t *cache_n;
     const uint8_t *cache_exh;
+    double *row_B;                 // [N] bound of the row's last (re)scan: a cache with fewer
+                                   // than k entries holds every eligible column with
+                                   // D <= row_B (+inf: unbounded; then cache_exh is set)
+    unsigned long long *comp_bound;   // [N] per component: D bits of some outgoing pair
+    const float *X;                // [N][d] the rows (exact distances of the bound search)
+    int d;
     unsigned long long *row_D;     // [N] key of the row's best outgoing candidate (D bits)
     unsigned long long *row_ab;    // [N] (min << 32) | max
     uint8_t *row_state;            // 0 none, 1 resolved, 2 unresolved (row_D/row_ab: bound)

@@ -34,19 +34,24 @@ cudaError_t launch_check_finite(const float *X, int64_t n, int *flag, cudaStream
 // ---------------------------------------------------------------------------------
 // Spatial order of the rows.  The sweeps read operands in an order where rows that are
 // close in space are close in memory, so that a row tile meets its near neighbours in
-// its first column tiles and far tiles can be bounded as a whole.  Rows are grouped by
-// their nearest landmark (L rows taken at regular strides), groups follow a nearest-
-// neighbour chain through the landmarks, and within a group rows are ordered by their
-// distance to the landmark, then by index: far outliers of a group end up in its last
-// tile.  The order only affects speed: every decision uses original indices
-// and the exact binary64 distance.
+// its first column tiles and far tiles can be bounded as a whole.
+//   - Landmarks: L rows taken at regular strides; every row joins the group of its
+//     nearest landmark.
+//   - Groups are ordered along a greedy nearest-neighbour chain through S <= 1024 coarse
+//     landmarks (also regular strides): a landmark follows the chain rank of its nearest
+//     coarse landmark, then its distance to it.
+//   - Within a group rows follow their distance to the landmark, then their index.
+//   - Rows much farther from their landmark than is typical (squared distance above 9
+//     times the median) are isolated points: they go, in the same order, after all
+//     other rows, so that they do not widen the tiles of the dense groups.
+// The order only affects speed: every decision uses original indices and the exact
+// binary64 distance.
 // ---------------------------------------------------------------------------------
 constexpr int kLandChunk = 128;
 constexpr int kMaxLandmarks = 1024;
 
-// Order of the landmark groups: a greedy nearest-neighbour chain through the landmarks
-// (start at landmark 0, always step to the nearest unvisited one), so that consecutive
-// groups are close in space.  One CTA; landmark m is row m*N/L.
+// Order of the coarse landmarks: a greedy nearest-neighbour chain (start at landmark 0,
+// always step to the nearest unvisited one).  One CTA; landmark m is row m*N/L.
 __global__ void __launch_bounds__(kMaxLandmarks) k_landmark_chain(const float *__restrict__ X, int64_t N, int d,
                                                                   int L, uint32_t *__restrict__ rank)
 {
@@ -113,25 +118,29 @@ cudaError_t launch_landmark_chain(const float *X, int64_t N, int d, int64_t L, u
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_landmark_keys(const float *__restrict__ X, int64_t N, int d, int64_t L,
-                                                       const uint32_t *__restrict__ rank, nnm_edge *__restrict__ keys)
+// For each query q < Q (row q*N/Q of X) the nearest of the R reference rows (row r*N/R)
+// by FP32 squared distance (first one on ties): index and value.
+__global__ void __launch_bounds__(256) k_nearest_ref(const float *__restrict__ X, int64_t N, int d, int64_t Q,
+                                                     int64_t R, uint32_t *__restrict__ arg_out,
+                                                     float *__restrict__ dist_out)
 {
-    __shared__ float lm[kLandChunk * 32];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ __align__(16) float lm[kLandChunk * 32];
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = q < Q ? q * N / Q : 0;
     float x[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) x[k] = (i < N && k < d) ? X[i * d + k] : 0.0f;
+    for (int k = 0; k < 32; ++k) x[k] = (q < Q && k < d) ? X[row * d + k] : 0.0f;
     float best = INFINITY;
     int64_t arg = 0;
-    for (int64_t m0 = 0; m0 < L; m0 += kLandChunk) {
+    for (int64_t m0 = 0; m0 < R; m0 += kLandChunk) {
         __syncthreads();
-        for (int q = threadIdx.x; q < kLandChunk * 32; q += blockDim.x) {
-            const int64_t m = m0 + q / 32;
-            const int k = q % 32;
-            lm[q] = (m < L && k < d) ? X[(m * N / L) * d + k] : 0.0f;
+        for (int t = threadIdx.x; t < kLandChunk * 32; t += blockDim.x) {
+            const int64_t m = m0 + t / 32;
+            const int k = t % 32;
+            lm[t] = (m < R && k < d) ? X[(m * N / R) * d + k] : 0.0f;
         }
         __syncthreads();
-        const int64_t cnt = L - m0 < kLandChunk ? L - m0 : kLandChunk;
+        const int64_t cnt = R - m0 < kLandChunk ? R - m0 : kLandChunk;
         for (int m = 0; m < cnt; ++m) {
             float acc = 0.0f;
 #pragma unroll
@@ -145,20 +154,98 @@ __global__ void __launch_bounds__(256) k_landmark_keys(const float *__restrict__
             }
         }
     }
-    if (i < N) {
-        nnm_edge e;
-        e.a = (uint32_t)i;
-        e.b = 0u;
-        e.D = (double)rank[arg] * 4294967296.0 + (double)__float_as_uint(best);   // exact: < 2^53
-        keys[i] = e;
+    if (q < Q) {
+        arg_out[q] = (uint32_t)arg;
+        dist_out[q] = best;
     }
 }
 
-cudaError_t launch_landmark_keys(const float *X, int64_t N, int d, int64_t L, const uint32_t *rank, nnm_edge *keys,
-                                 cudaStream_t s)
+cudaError_t launch_nearest_ref(const float *X, int64_t N, int d, int64_t Q, int64_t R, uint32_t *arg, float *dist,
+                               cudaStream_t s)
 {
-    k_landmark_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(X, N, d, L, rank, keys);
+    k_nearest_ref<<<(unsigned)((Q + 255) / 256), 256, 0, s>>>(X, N, d, Q, R, arg, dist);
     count_launches(1);
+    return cudaGetLastError();
+}
+
+// Histogram of the squared distances to the landmarks by their top 12 bits (exponent and
+// three mantissa bits), for the median.
+constexpr int kHistBins = 4096;
+
+__global__ void __launch_bounds__(256) k_dist_hist(const float *__restrict__ dist, int64_t n,
+                                                   unsigned int *__restrict__ hist)
+{
+    __shared__ unsigned int h[kHistBins];
+    for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) h[b] = 0u;
+    __syncthreads();
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[__float_as_uint(dist[q]) >> 20], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kHistBins; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// Isolation threshold: 9 times the upper edge of the median's bin.
+__global__ void k_dist_tau(const unsigned int *__restrict__ hist, int64_t n, float *__restrict__ tau)
+{
+    if (threadIdx.x != 0) return;
+    unsigned long long run = 0;
+    int b = 0;
+    for (; b < kHistBins; ++b) {
+        run += hist[b];
+        if (2 * run >= (unsigned long long)n) break;
+    }
+    const float edge = b + 1 < 2040 ? __uint_as_float((unsigned int)(b + 1) << 20) : INFINITY;
+    *tau = 9.0f * edge;
+}
+
+// Sort keys of the landmarks: (chain rank of the nearest coarse landmark, distance).
+__global__ void k_landmark_keys(const uint32_t *__restrict__ arg, const float *__restrict__ dist, int64_t L,
+                                const uint32_t *__restrict__ crank, nnm_edge *__restrict__ keys)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= L) return;
+    nnm_edge e;
+    e.a = (uint32_t)m;
+    e.b = 0u;
+    e.D = (double)crank[arg[m]] * 4294967296.0 + (double)__float_as_uint(dist[m]);   // exact: < 2^53
+    keys[m] = e;
+}
+
+// Sort keys of the rows: (isolated, rank of the landmark group, distance).
+__global__ void k_row_keys(const uint32_t *__restrict__ arg, const float *__restrict__ dist, int64_t N,
+                           const uint32_t *__restrict__ lrank, const float *__restrict__ tau,
+                           nnm_edge *__restrict__ keys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float v = dist[i];
+    const double far = v > *tau ? 8192.0 : 0.0;   // above every group rank (< 4096)
+    nnm_edge e;
+    e.a = (uint32_t)i;
+    e.b = 0u;
+    e.D = (far + (double)lrank[arg[i]]) * 4294967296.0 + (double)__float_as_uint(v);   // exact: < 2^53
+    keys[i] = e;
+}
+
+cudaError_t launch_spatial_keys(const uint32_t *larg, const float *ldist, int64_t L, const uint32_t *crank,
+                                const uint32_t *rarg, const float *rdist, int64_t N, const uint32_t *lrank,
+                                unsigned int *hist, float *tau, nnm_edge *lkeys, nnm_edge *rkeys, int which,
+                                cudaStream_t s)
+{
+    if (which == 0) {
+        k_landmark_keys<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(larg, ldist, L, crank, lkeys);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(hist, 0, kHistBins * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
+    int blocks = (int)((N + 255) / 256);
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    k_dist_hist<<<blocks, 256, 0, s>>>(rdist, N, hist);
+    k_dist_tau<<<1, 32, 0, s>>>(hist, N, tau);
+    k_row_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rarg, rdist, N, lrank, tau, rkeys);
+    count_launches(3);
     return cudaGetLastError();
 }
 

@@ -20,16 +20,6 @@ namespace {
 
 constexpr int kFinWarps = 4;
 
-__device__ __forceinline__ double canon_D(const float *__restrict__ xi, const float *__restrict__ xj, int d)
-{
-    double s = 0.0;
-    for (int k = 0; k < d; ++k) {
-        const double e = __dsub_rn((double)xi[k], (double)xj[k]);
-        s = __dadd_rn(s, __dmul_rn(e, e));
-    }
-    return s;
-}
-
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v)
 {
     if (p) atomicMax(p, (unsigned long long)__double_as_longlong(v));
@@ -204,7 +194,11 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
         if (lane == 0) wD[b.e] = INFINITY;
         __syncwarp();
     }
-    const double T = threshold(a.m, i, taken < a.k ? INFINITY : (float)vk);
+    // a bounded row needs only columns with D <= B: their candidate values are at most
+    // the threshold of the value B (in candidate units)
+    const double B = a.row_B ? a.row_B[i] : INFINITY;
+    double T = threshold(a.m, i, taken < a.k ? INFINITY : (float)vk);
+    if (B < INFINITY) T = fmin(T, threshold(a.m, i, __double2float_ru(B / a.m.inv_scale2)));
     const bool any_ovf = __any_sync(0xffffffffu, ovf);
     if (lane == 0) {
         a.ovf_flag[q] = any_ovf ? 1 : 0;
@@ -215,6 +209,11 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     for (int e = lane; e < n_ent; e += 32) wD[e] = (wj[e] != kInvalid && (double)wv[e] <= T) ? 0.0 : INFINITY;
     __syncwarp();
     const int nc = exact_distances(xi, a.X, a.d, wD, wj, n_ent, a.k, a.m, a.m.tensor != 0);
+    if (B < INFINITY) {
+        for (int e = lane; e < n_ent; e += 32)
+            if (wD[e] > B) wD[e] = INFINITY;
+        __syncwarp();
+    }
     double emax_abs = 0.0, emax_rel = 0.0;
     for (int e = lane; e < n_ent; e += 32) {
         if (wD[e] < INFINITY) {
@@ -232,8 +231,9 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     }
     if (lane == 0) {
         if (a.res_n) a.res_n[i] = (uint8_t)n_out;
-        // fewer than k results means every eligible column was among the candidates
-        if (a.res_exh) a.res_exh[i] = (uint8_t)(n_out < a.k);
+        // fewer than k results from an unbounded row means every eligible column was
+        // among the candidates
+        if (a.res_exh) a.res_exh[i] = (uint8_t)(n_out < a.k && !(B < INFINITY));
         atomic_max_nonneg(a.st_max_abs, emax_abs);
         atomic_max_nonneg(a.st_max_rel, emax_rel);
         if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nc);
@@ -269,12 +269,16 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
     __syncwarp();
     __threadfence_block();
     const int nd = exact_distances(xi, a.X, a.d, wD, wj, (int)cnt, a.k, a.m, true);
+    const double B = a.row_B ? a.row_B[i] : INFINITY;
+    if (B < INFINITY)
+        for (uint32_t e = lane; e < cnt; e += 32)
+            if (wD[e] > B) wD[e] = INFINITY;
     __threadfence_block();
     int n_out;
     select_topk(wD, wj, (int)cnt, a.k, i, a.res_j, a.res_D, &n_out);
     if (lane == 0) {
         if (a.res_n) a.res_n[i] = (uint8_t)n_out;
-        if (a.res_exh) a.res_exh[i] = (uint8_t)((int)cnt < a.k);
+        if (a.res_exh) a.res_exh[i] = (uint8_t)((int)cnt < a.k && !(B < INFINITY));
         if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nd);
         if (a.st_max_cand) atomicMax(a.st_max_cand, (unsigned long long)cnt);
     }

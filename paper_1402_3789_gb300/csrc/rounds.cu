@@ -14,6 +14,13 @@
 // whose whole cache lies inside its component only bounds its answer from below (by
 // its last cached key); it is rescanned only if that bound is below its component's
 // best resolved key.
+//
+// A rescan only has to find outgoing pairs that could still be the component's
+// minimum, so it is bounded by an exact D that some outgoing pair of the component
+// already has: the best resolved one, or one found by the flagged rows themselves
+// among their neighbours in the spatial order of the operands.  A bounded rescan
+// caches the k nearest eligible columns with D <= bound; when fewer than k exist, every
+// other eligible column has D > bound, which is the row's new lower bound.
 #include "nnm_internal.cuh"
 
 namespace nnm {
@@ -47,6 +54,7 @@ __global__ void k_round_init(RoundState st)
     st.comp[i] = (uint32_t)i;
     st.parent[i] = (uint32_t)i;
     st.frozen[i] = 0;
+    st.row_B[i] = INFINITY;
 }
 
 // Per row: the key of its nearest neighbour outside its component, from the cache.
@@ -72,8 +80,20 @@ __global__ void k_resolve(RoundState st, const uint32_t *__restrict__ rows, int6
             return;
         }
     }
-    if (st.cache_exh[i] || n == 0) {
-        st.row_state[i] = 0;
+    if (st.cache_exh[i]) {
+        st.row_state[i] = 0;   // every eligible column was cached: none is outside
+        return;
+    }
+    if (n < st.k) {
+        // bounded scan: every column not cached has D > row_B
+        const double B = st.row_B[i];
+        if (!(B < INFINITY)) {
+            st.row_state[i] = 0;
+            return;
+        }
+        st.row_D[i] = (unsigned long long)__double_as_longlong(B);
+        st.row_ab[i] = kMaxKey;
+        st.row_state[i] = 2;
         return;
     }
     // lower bound: every column not cached has a larger key than the last cached one
@@ -88,6 +108,7 @@ __global__ void k_best_reset(RoundState st)
     if (i >= st.N) return;
     st.best_D[i] = kMaxKey;
     st.best_ab[i] = kMaxKey;
+    st.comp_bound[i] = (unsigned long long)__double_as_longlong(INFINITY);
 }
 
 __global__ void k_best_d(RoundState st)
@@ -105,16 +126,35 @@ __global__ void k_best_ab(RoundState st)
     if (st.row_D[i] == st.best_D[c]) atomicMin(&st.best_ab[c], st.row_ab[i]);
 }
 
+constexpr int kNeighbourSearch = 16;   // positions searched on each side
+
 __global__ void k_flag(RoundState st)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= st.N) return;
     uint8_t f = 0;
+    const uint32_t p = st.row2pos[i];
     if (st.row_state[i] == 2) {
         const uint32_t c = st.comp[i];
         f = key_less(st.row_D[i], st.row_ab[i], st.best_D[c], st.best_ab[c]);
+        if (f) {
+            // the nearest positions outside the component on either side give outgoing
+            // pairs, whose exact D bound the component's minimum from above
+            const float *xi = st.X + i * st.d;
+            for (int side = -1; side <= 1; side += 2) {
+                for (int s = 1; s <= kNeighbourSearch; ++s) {
+                    const int64_t q = (int64_t)p + side * s;
+                    if (q < 0 || q >= st.N) break;
+                    const uint32_t j = st.pos2row[q];
+                    if (st.comp[j] == c) continue;
+                    const double D = canon_D(xi, st.X + (int64_t)j * st.d, st.d);
+                    atomicMin(&st.comp_bound[c], (unsigned long long)__double_as_longlong(D));
+                    break;
+                }
+            }
+        }
     }
-    st.flag_pos[st.row2pos[i]] = f;
+    st.flag_pos[p] = f;
 }
 
 // Rescan rows in increasing position (so that a row tile of a rescan is spatially
@@ -163,8 +203,15 @@ __global__ void __launch_bounds__(kCompact) k_compact_scatter(RoundState st)
     __syncthreads();
     if (f) {
         const uint32_t r = st.block_cnt[blockIdx.x] + ws[w] + __popc(bal & ((1u << lane) - 1u));
+        const uint32_t i = st.pos2row[p];
         st.list_pos[r] = (uint32_t)p;
-        st.list[r] = st.pos2row[p];
+        st.list[r] = i;
+        // the rescan bound: the smaller of the best resolved D and the neighbour bound
+        const uint32_t c = st.comp[i];
+        const unsigned long long bd = st.best_D[c];
+        double B = bd == kMaxKey ? INFINITY : __longlong_as_double((long long)bd);
+        B = fmin(B, __longlong_as_double((long long)st.comp_bound[c]));
+        st.row_B[i] = B;
     }
 }
 

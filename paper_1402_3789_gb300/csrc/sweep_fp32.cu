@@ -66,7 +66,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     const int64_t t_begin = (int64_t)split * tps;
     const int64_t t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
     const int64_t ntiles = t_end > t_begin ? t_end - t_begin : 0;
-    auto tile_col = [&](int64_t tile) -> int64_t { return ((tile0 + t_begin + tile) % ntile_all) * kTile; };
+    const int64_t start = (tile0 + t_begin) % ntile_all;
+    auto tile_col = [&](int64_t tile) -> int64_t {
+        const int64_t x = start + tile;
+        return (x >= ntile_all ? x - ntile_all : x) * kTile;
+    };
 
     // operand rows hold a.dp floats; the tile keeps DP >= a.dp per column (rest zero)
     if (a.dp < DP)
@@ -181,6 +185,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     };
     // Thresholds already published for these rows by other column ranges; a collect pass
     // knows its thresholds from the start.
+    if (!COLLECT && a.row_B) {
+        // a bounded row starts at the threshold of its bound
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            if (!valid[r]) continue;
+            const double B = a.row_B[a.pos2row[row[r]]];
+            if (B < INFINITY) sel[r].bound(sel_threshold(a.sc, rc, __double2float_ru(B / a.m.inv_scale2)));
+        }
+    }
     if (!COLLECT && a.splits > 1) {
 #pragma unroll
         for (int r = 0; r < 2; ++r)

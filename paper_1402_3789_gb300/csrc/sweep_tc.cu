@@ -229,13 +229,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     // Column tiles in the order of the operands, starting at this row tile's own place
     // and wrapping around: near neighbours come first, so thresholds fall early.  Split
     // s takes the s-th range of that cyclic order.
-    const int64_t ntile_all = (a.N + kBN - 1) / kBN;
-    const int64_t tile0 = (int64_t)(a.rows ? a.rows[slot0] : (uint32_t)slot0) / kBN;
-    const int64_t tps = a.cols_per_split / kBN;
-    const int64_t t_begin = (int64_t)split * tps;
-    const int64_t t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
-    const int ntiles = t_end > t_begin ? (int)(t_end - t_begin) : 0;
-    auto tile_col = [&](int t) -> int64_t { return ((tile0 + t_begin + t) % ntile_all) * kBN; };
+    const int ntile_all = (int)((a.N + kBN - 1) / kBN);
+    const int tile0 = (int)((a.rows ? a.rows[slot0] : (uint32_t)slot0) / kBN);
+    const int tps = (int)(a.cols_per_split / kBN);
+    const int t_begin = split * tps;
+    const int t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
+    const int ntiles = t_end > t_begin ? t_end - t_begin : 0;
+    const int start = (tile0 + t_begin) % ntile_all;
+    auto col_tile = [&](int t) -> int { return start + t >= ntile_all ? start + t - ntile_all : start + t; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -328,46 +329,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         // The kept tiles' numbers travel with the stages; -1 ends the sequence.
         const float rhoR = sphere_slack(__uint_as_float(sh->rho_bits), __uint_as_float(sh->ymax_bits));
         int issued = 0, skipped = 0;
-        bool stop = false;
-        // lower bounds of 32 consecutive tiles at a time, one per lane (they do not depend
-        // on the thresholds, which are read fresh at each decision)
-        int lb_base = -32;
-        float lb_lane = -INFINITY;
-        for (int t = 0; t <= ntiles && !stop; ++t) {
-            const bool last = t == ntiles;
-            const int64_t col = last ? -1 : tile_col(t);
-            int keep = 1;
-            if (!last && a.prune) {
-                if (t >= lb_base + 32) {
-                    lb_base = t;
-                    lb_lane = -INFINITY;
-                    if (t + lane < ntiles) {
-                        const int64_t ct = tile_col(t + lane) / kBN;
-                        lb_lane = tile_lower_bound(sh->cR, rhoR, a.tile_c + ct * a.d, a.tile_rho[ct], a.d, a.lb_R2,
-                                                   a.lb_eps, a.lb_gamma);
-                    }
-                }
-                const float lb = __shfl_sync(0xffffffffu, lb_lane, t - lb_base);
-                if (lane == 0) {
-                    float thr = -INFINITY;
-                    for (int w = 0; w < kEpiWarps; ++w) thr = fmaxf(thr, ((volatile float *)sh->warp_thr)[w]);
-                    keep = !(lb > thr);
-                }
-            }
-            keep = __shfl_sync(0xffffffffu, keep, 0);
-            if (a.prune && t == 1 && lane == 0) {
-                // Every later decision waits for the thresholds the epilogue learns from the
-                // first tile (the nearest columns), not for the initial "none yet": one tile
-                // of pipeline fill per CTA.  Bounded; on time-out the decisions only get
-                // less selective.
-                const uint64_t t0 = global_ns();
-                while (((volatile int *)&sh->npub)[0] < kEpiWarps && !*abort_flag && global_ns() - t0 < kWaitNs)
-                    __nanosleep(64);
-            }
-            if (!keep) {
-                ++skipped;
-                continue;
-            }
+        bool ok_all = true;
+        // stage the column tile ct (-1: the end marker) into the next slot of the ring
+        auto issue = [&](int ct) -> bool {
             const int s = issued % kStages;
             int ok = 1;
             if (lane == 0 && issued >= kStages)
@@ -375,21 +339,64 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) {
                 *abort_flag = 1;
-                break;
+                return false;
             }
             if (lane == 0) {
-                sh->ring_tile[s] = last ? -1 : (int)(col / kBN);
-                if (last) {
+                sh->ring_tile[s] = ct;
+                if (ct < 0) {
                     mbar_arrive(&sh->full[s]);
                 } else {
                     mbar_arrive_expect_tx(&sh->full[s], b_bytes);
-                    bulk_g2s(sB + (size_t)s * b_bytes, a.XB + col * kpad, b_bytes, &sh->full[s]);
+                    bulk_g2s(sB + (size_t)s * b_bytes, a.XB + (int64_t)ct * kBN * kpad, b_bytes, &sh->full[s]);
                 }
             }
             ++issued;
-            stop = last;
+            __syncwarp();
+            return true;
+        };
+        int t = 0;
+        if (a.prune) {
+            // Without thresholds known at the start, the first tile (the nearest columns)
+            // goes unconditionally and every later decision waits for the thresholds the
+            // epilogue learns from it: one tile of pipeline fill per CTA.  The wait is
+            // bounded; on time-out the decisions only get less selective.
+            if (!(COLLECT || a.row_B) && ntiles > 0) {
+                ok_all = issue(col_tile(0));
+                t = 1;
+            }
+            if (ok_all && t < ntiles && lane == 0) {
+                const uint64_t t0 = global_ns();
+                while (((volatile int *)&sh->npub)[0] < kEpiWarps && !*abort_flag && global_ns() - t0 < kWaitNs)
+                    __nanosleep(64);
+            }
             __syncwarp();
         }
+        // 32 tiles per step: one lower bound per lane against one snapshot of the rows'
+        // largest threshold (thresholds only fall, so a stale one only keeps more)
+        while (ok_all && t < ntiles) {
+            const int n = ntiles - t < 32 ? ntiles - t : 32;
+            unsigned int keepm = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+            if (a.prune) {
+                float lb = -INFINITY;
+                if (lane < n) {
+                    const int ct = col_tile(t + lane);
+                    lb = tile_lower_bound(sh->cR, rhoR, a.tile_c + (int64_t)ct * a.d, a.tile_rho[ct], a.d, a.lb_R2,
+                                          a.lb_eps, a.lb_gamma);
+                }
+                float thr = lane < kEpiWarps ? ((volatile float *)sh->warp_thr)[lane] : -INFINITY;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) thr = fmaxf(thr, __shfl_xor_sync(0xffffffffu, thr, o));
+                keepm = __ballot_sync(0xffffffffu, lane < n && !(lb > thr));
+                skipped += n - __popc(keepm);
+            }
+            while (keepm) {
+                const int q = __ffs(keepm) - 1;
+                keepm &= keepm - 1u;
+                if (!(ok_all = issue(col_tile(t + q)))) break;
+            }
+            t += n;
+        }
+        if (ok_all) issue(-1);
         if (lane == 0 && a.st_tiles) {
             atomicAdd(&a.st_tiles[0], (unsigned long long)skipped);
             atomicAdd(&a.st_tiles[1], (unsigned long long)(issued > 0 ? issued - 1 : 0));
@@ -469,8 +476,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         uint32_t *bj = band_j + threadIdx.x;
         float *stg = stage_v + threadIdx.x * kStageStride;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
-        // Thresholds already published for these rows by other column ranges, then the
-        // warp's first publication (a collect pass knows its thresholds from the start).
+        // A bounded row starts at the threshold of its bound; thresholds already published
+        // for these rows by other column ranges apply too.  Then the warp's first
+        // publication: before the first tile when the thresholds are known from the start
+        // (collect pass, bounded rows), else after it.
+        if (!COLLECT && valid && a.row_B) {
+            const double B = a.row_B[a.pos2row[myrow]];
+            if (B < INFINITY) sel.bound(sel_threshold(a.sc, rc, __double2float_ru(B / a.m.inv_scale2)));
+        }
         if (!COLLECT && a.splits > 1 && valid) sel.bound(shared_thr_exchange(&a.slot_thr[slot0 + myrow_slot], INFINITY));
         auto publish = [&]() {
             float wt = COLLECT ? cthr : sel.thr;
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             if (lane == 0) ((volatile float *)sh->warp_thr)[warp] = wt;
         };
         bool published = false;
-        if (a.prune && COLLECT) {
+        if (a.prune && (COLLECT || a.row_B)) {
             publish();
             __syncwarp();
             if (lane == 0) atomicAdd(&sh->npub, 1);
