@@ -15,8 +15,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "nnm_internal.cuh"
 
@@ -47,8 +49,8 @@ struct nnm_ctx {
     Margin margin{};
     SelConst selc{};
     // spatial order of the operands (see prep.cu) and the column tiles' bounding spheres
-    uint32_t *pos2row = nullptr, *row2pos = nullptr, *list_pos = nullptr;
-    float *tile_c = nullptr, *tile_rho = nullptr, *mu_f = nullptr;
+    uint32_t *pos2row = nullptr, *row2pos = nullptr, *list_pos = nullptr, *group = nullptr;
+    float *tile_c = nullptr, *tile_rho = nullptr, *mu_f = nullptr, *blk_c = nullptr, *blk_rho = nullptr;
     int tile_w = 0;
     float lb_R2 = 0.f, lb_eps = 0.f, lb_gamma = 0.f;
     // operands
@@ -79,6 +81,7 @@ struct nnm_ctx {
     uint8_t *cache_n = nullptr, *cache_exh = nullptr;
     double *row_B = nullptr;
     unsigned long long *comp_bound = nullptr;
+    uint32_t *comp_pos = nullptr, *tile_comp = nullptr;
     uint32_t *comp = nullptr, *parent = nullptr, *list = nullptr;
     unsigned long long *row_D = nullptr, *row_ab = nullptr, *best_D = nullptr, *best_ab = nullptr;
     uint8_t *row_state = nullptr, *frozen = nullptr, *flag_pos = nullptr;
@@ -189,7 +192,8 @@ int choose_splits(const nnm_ctx *c, int64_t nslots)
     const int64_t row_ctas = (nslots + kRowTile - 1) / kRowTile;
     const int64_t target = is_tensor(c) ? 152 * 4 : 152 * 2 * 4;
     int64_t s = (target + row_ctas - 1) / row_ctas;
-    const int64_t max_by_cols = (c->N + 2047) / 2048;   // at least 16 tiles per range
+    // at least 32 tiles of 64 columns per range (FP32), one block of 32 tiles of 128 (tensor)
+    const int64_t max_by_cols = is_tensor(c) ? (c->N + 4095) / 4096 : (c->N + 2047) / 2048;
     if (s > max_by_cols) s = max_by_cols;
     if (s > kMaxSplits) s = kMaxSplits;
     if (s < 1) s = 1;
@@ -284,6 +288,9 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.tile_w = c->tile_w;
     a.tile_c = c->tile_c;
     a.tile_rho = c->tile_rho;
+    a.group = c->group;
+    a.blk_c = c->blk_c;
+    a.blk_rho = c->blk_rho;
     a.mu_f = c->mu_f;
     a.scale_f = (float)c->scale;
     a.lb_R2 = c->lb_R2;
@@ -346,6 +353,8 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
             ca.rows = rows + b0;
             ca.nslots = nb;
             ca.comp = comp;
+            ca.comp_pos = comp ? c->comp_pos : nullptr;
+            ca.tile_comp = comp ? c->tile_comp : nullptr;
             const int S2 = choose_splits(c, nb);
             ca.cols_per_split = round_up((c->N + S2 - 1) / S2, 128);
             ca.splits = (int)((c->N + ca.cols_per_split - 1) / ca.cols_per_split);
@@ -425,6 +434,8 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     sa.rows = rows;
     sa.nslots = nslots;
     sa.comp = comp;
+    sa.comp_pos = comp ? c->comp_pos : nullptr;
+    sa.tile_comp = comp ? c->tile_comp : nullptr;
     sa.cols_per_split = cps;
     sa.splits = splits;
     sa.out_v = c->cand_v;
@@ -549,6 +560,7 @@ nnm_status prepare(nnm_ctx *c)
         NNM_TRY(dalloc(c, &c->pos2row, (size_t)c->N));
         NNM_TRY(dalloc(c, &c->row2pos, (size_t)c->N));
         NNM_TRY(dalloc(c, &c->list_pos, (size_t)c->N));
+        NNM_TRY(dalloc(c, &c->group, (size_t)c->N));
         int64_t L = c->N / 512;
         if (L > kMaxGroups) L = kMaxGroups;
         if (L < 1) L = 1;
@@ -599,13 +611,13 @@ nnm_status prepare(nnm_ctx *c)
             e = launch_spatial_keys(larg, ldist, L, crank, nullptr, nullptr, 0, nullptr, nullptr, nullptr, lkeys,
                                     nullptr, 0, s);
         if (e == cudaSuccess) e = launch_sort_edges(lkeys, ltmp, L, s, &lsorted);
-        if (e == cudaSuccess) e = launch_order_from_keys(lsorted, L, lpos, lrank, s);
+        if (e == cudaSuccess) e = launch_order_from_keys(lsorted, L, lpos, lrank, nullptr, s);
         if (e == cudaSuccess) e = launch_nearest_ref(c->X, c->N, c->d, c->N, L, rarg, rdist, s);
         if (e == cudaSuccess)
             e = launch_spatial_keys(nullptr, nullptr, 0, nullptr, rarg, rdist, c->N, lrank, hist, tau, nullptr, keys, 1,
                                     s);
         if (e == cudaSuccess) e = launch_sort_edges(keys, tmp, c->N, s, &sorted);
-        if (e == cudaSuccess) e = launch_order_from_keys(sorted, c->N, c->pos2row, c->row2pos, s);
+        if (e == cudaSuccess) e = launch_order_from_keys(sorted, c->N, c->pos2row, c->row2pos, c->group, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         free_all();
         if (e != cudaSuccess) return fail(c, NNM_ECUDA, "spatial order: %s", cudaGetErrorString(e));
@@ -683,10 +695,14 @@ nnm_status prepare(nnm_ctx *c)
     // bounding spheres of the column tiles and the constants of their lower bound
     {
         const int64_t nt = (c->N + c->tile_w - 1) / c->tile_w;
-        NNM_TRY(dalloc(c, &c->tile_c, (size_t)nt * c->d));
-        NNM_TRY(dalloc(c, &c->tile_rho, (size_t)nt));
-        NNM_CUDA(c, launch_tile_spheres(c->X, c->N, c->d, c->pos2row, c->mu_f, (float)c->scale, c->tile_w, c->tile_c,
-                                        c->tile_rho, s));
+        NNM_TRY(dalloc(c, &c->tile_c, (size_t)nt * 2 * c->d));
+        NNM_TRY(dalloc(c, &c->tile_rho, (size_t)nt * 2));
+        NNM_CUDA(c, launch_tile_spheres(c->X, c->N, c->d, c->pos2row, c->group, c->mu_f, (float)c->scale, c->tile_w,
+                                        c->tile_c, c->tile_rho, s));
+        const int64_t nb = (nt + 31) / 32;
+        NNM_TRY(dalloc(c, &c->blk_c, (size_t)nb * c->d));
+        NNM_TRY(dalloc(c, &c->blk_rho, (size_t)nb));
+        NNM_CUDA(c, launch_block_spheres(c->tile_c, c->tile_rho, nt, c->d, c->blk_c, c->blk_rho, s));
         const double grow = 1.0 + 0x1p-20;
         if (is_tensor(c)) {
             c->lb_R2 = up_f(2.0 * c->margin.R * grow);
@@ -712,6 +728,8 @@ nnm_status ensure_rounds(nnm_ctx *c)
     NNM_TRY(dalloc(c, &c->cache_exh, (size_t)N));
     NNM_TRY(dalloc(c, &c->row_B, (size_t)N));
     NNM_TRY(dalloc(c, &c->comp_bound, (size_t)N));
+    NNM_TRY(dalloc(c, &c->comp_pos, (size_t)N));
+    NNM_TRY(dalloc(c, &c->tile_comp, (size_t)((N + c->tile_w - 1) / c->tile_w)));
     NNM_TRY(dalloc(c, &c->parent, (size_t)N));
     NNM_TRY(dalloc(c, &c->list, (size_t)N));
     NNM_TRY(dalloc(c, &c->row_D, (size_t)N));
@@ -761,6 +779,7 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     st.cache_exh = c->cache_exh;
     st.row_B = c->row_B;
     st.comp_bound = c->comp_bound;
+    st.overscan = getenv("NNM_OVERSCAN") ? atof(getenv("NNM_OVERSCAN")) : 1.0;
     st.X = c->X;
     st.d = c->d;
     st.row_D = c->row_D;
@@ -812,8 +831,19 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
             NNM_CUDA(c, launch_flag_rescans(st, s));
         }
         NNM_TRY(read_dev(c, &nres, &c->dcount[1]));
+        std::vector<double> trace_B;
+        if (trace && nres > 0) {
+            // rescan bounds of the flagged rows
+            std::vector<uint32_t> lst(nres);
+            std::vector<double> rb(c->N);
+            cudaMemcpyAsync(lst.data(), c->list, nres * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(rb.data(), c->row_B, c->N * sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            for (uint32_t q = 0; q < nres; ++q) trace_B.push_back(rb[lst[q]]);
+        }
         if (nres > 0) {
             c->stats.rows_rescanned += nres;
+            NNM_CUDA(c, launch_position_comps(st, c->tile_w, c->comp_pos, c->tile_comp, s));
             NNM_TRY(run_knn(c, c->list_pos, nres, c->kc, c->comp, c->cache_j, c->cache_D, c->cache_n, c->cache_exh,
                             false, c->row_B));
             Phase ph(c, &c->stats.ms_rounds);
@@ -847,6 +877,14 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
                             "edges %u, components %lld\n",
                     round, nres, c->stats.ms_sweep - sweep0, c->stats.ms_rerank - rerank0, t1[1] - t0[1],
                     t1[0] - t0[0], nedge, (long long)ncomp);
+            if (!trace_B.empty()) {
+                std::sort(trace_B.begin(), trace_B.end());
+                const size_t m = trace_B.size();
+                size_t ninf = 0;
+                for (double b : trace_B) ninf += !(b < INFINITY);
+                fprintf(stderr, "    rescan bounds: unbounded %zu, quantiles 10/50/90%%: %.4g %.4g %.4g\n", ninf,
+                        trace_B[m / 10], trace_B[m / 2], trace_B[(9 * m) / 10]);
+            }
         }
     }
     uint32_t ne = 0;
@@ -1022,6 +1060,9 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->pos2row);
     dfree(c->tile_c);
     dfree(c->tile_rho);
+    dfree(c->group);
+    dfree(c->blk_c);
+    dfree(c->blk_rho);
     dfree(c->mu_f);
     dfree(c->row2pos);
     dfree(c->list_pos);
@@ -1055,6 +1096,8 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->cache_exh);
     dfree(c->row_B);
     dfree(c->comp_bound);
+    dfree(c->comp_pos);
+    dfree(c->tile_comp);
     dfree(c->comp);
     dfree(c->parent);
     dfree(c->list);

@@ -77,6 +77,9 @@ struct SweepArgs {
     // rows and columns are positions in the spatial order of the operands
     const uint32_t *rows;     // slot -> row position (nullptr: slot q is position q)
     int64_t nslots;
+    const uint32_t *comp_pos;   // with comp: component of each position
+    const uint32_t *tile_comp;  // with comp: component of each column tile of tile_w
+                                // positions when they all share one, else kInvalid
     const double *row_B;      // per original row: only columns with exact D <= row_B are
                               // wanted (nullptr: no bound); a bound lowers the starting
                               // threshold of the row
@@ -105,8 +108,11 @@ struct SweepArgs {
     // y = (x - mu_f) * scale_f, and the constants of the lower bound on candidate values
     int prune;
     int tile_w;
-    const float *tile_c;      // [ntiles][d]
-    const float *tile_rho;    // [ntiles]
+    const float *tile_c;      // [ntiles][2][d] two spheres per tile (split at a group change)
+    const float *tile_rho;    // [ntiles][2] (-1: empty part)
+    const uint32_t *group;    // [N] landmark group of each position (row tiles split alike)
+    const float *blk_c;       // tensor path: [nblocks][d] sphere of each block of 32 tiles
+    const float *blk_rho;     // [nblocks]
     const float *mu_f;        // [d] (nullptr: 0)
     float scale_f;
     float lb_R2;              // tensor: 2 * max rounding radius (scaled); FP32: 0
@@ -237,7 +243,7 @@ cudaError_t launch_spatial_keys(const uint32_t *larg, const float *ldist, int64_
                                 unsigned int *hist, float *tau, nnm_edge *lkeys, nnm_edge *rkeys, int which,
                                 cudaStream_t s);
 cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,
-                                   cudaStream_t s);
+                                   uint32_t *group /* nullable: landmark group per position */, cudaStream_t s);
 // out[q] = map[in[q]]
 cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *map, int64_t n, uint32_t *out, cudaStream_t s);
 // Ordered compaction: for every q < n with flag[q] != 0, in increasing q, append
@@ -258,8 +264,12 @@ cudaError_t launch_max_sqnorm(const float *X, int64_t N, int d, const double *mu
                               unsigned long long *out_bits, cudaStream_t s);
 // operands written at each row's position; r, P, E stay indexed by original row
 // Bounding spheres of the column tiles (tile_w consecutive positions).
-cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const float *mu_f,
-                                float scale_f, int tile_w, float *tile_c, float *tile_rho, cudaStream_t s);
+// Bounding spheres of blocks of 32 consecutive tiles, from the tiles' two spheres each.
+cudaError_t launch_block_spheres(const float *tile_c, const float *tile_rho, int64_t ntiles, int d, float *blk_c,
+                                 float *blk_rho, cudaStream_t s);
+cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const uint32_t *group,
+                                const float *mu_f, float scale_f, int tile_w, float *tile_c, float *tile_rho,
+                                cudaStream_t s);
 cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale,
                                int fp16, int terms, int kpad, int64_t Npad, const uint32_t *row2pos, uint16_t *XA,
                                uint16_t *XB,
@@ -282,6 +292,7 @@ struct RoundState {
                                    // than k entries holds every eligible column with
                                    // D <= row_B (+inf: unbounded; then cache_exh is set)
     unsigned long long *comp_bound;   // [N] per component: D bits of some outgoing pair
+    double overscan;               // rescan bound = overscan * the component's bound
     const float *X;                // [N][d] the rows (exact distances of the bound search)
     int d;
     unsigned long long *row_D;     // [N] key of the row's best outgoing candidate (D bits)
@@ -308,6 +319,10 @@ cudaError_t launch_flag_rescans(RoundState &st, cudaStream_t s);
 cudaError_t launch_hook(RoundState &st, cudaStream_t s);
 cudaError_t launch_jump(RoundState &st, cudaStream_t s);
 cudaError_t launch_relabel(RoundState &st, cudaStream_t s);
+// comp_pos[p] = comp[pos2row[p]]; tile_comp[t] = the component of tile t (tile_w
+// consecutive positions) if it is one for the whole tile, else kInvalid
+cudaError_t launch_position_comps(const RoundState &st, int tile_w, uint32_t *comp_pos, uint32_t *tile_comp,
+                                  cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // Sort (K6), restriction walk (K7), labels (K8)

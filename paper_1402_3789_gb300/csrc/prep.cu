@@ -250,19 +250,20 @@ cudaError_t launch_spatial_keys(const uint32_t *larg, const float *ldist, int64_
 }
 
 __global__ void k_order_from_keys(const nnm_edge *__restrict__ keys, int64_t N, uint32_t *pos2row,
-                                  uint32_t *row2pos)
+                                  uint32_t *row2pos, uint32_t *group)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const uint32_t i = keys[p].a;
     pos2row[p] = i;
     row2pos[i] = (uint32_t)p;
+    if (group) group[p] = (uint32_t)(keys[p].D * 0x1p-32);   // the key's high part: its group
 }
 
 cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,
-                                   cudaStream_t s)
+                                   uint32_t *group, cudaStream_t s)
 {
-    k_order_from_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(keys, N, pos2row, row2pos);
+    k_order_from_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(keys, N, pos2row, row2pos, group);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -394,23 +395,29 @@ cudaError_t launch_gather_f32(const uint32_t *in, const float *map, int64_t n, f
     return cudaGetLastError();
 }
 
-// One block per column tile: centroid (mean) of y = (x - mu_f) * scale_f over the
-// tile's positions, radius = largest distance to it, enlarged by sphere_slack.
+// One block per column tile.  The tile's positions split where their landmark group
+// first changes (part 0: the first group, part 1: the rest, possibly empty): two
+// bounding spheres, each the centroid (mean) of y = (x - mu_f) * scale_f over its part
+// and the largest distance to it, enlarged by sphere_slack (radius -1: empty part).
+// A tile that straddles two groups is then bounded by two tight spheres, not one wide one.
 __global__ void __launch_bounds__(128) k_tile_spheres(const float *__restrict__ X, int64_t N, int d,
                                                       const uint32_t *__restrict__ pos2row,
+                                                      const uint32_t *__restrict__ group,
                                                       const float *__restrict__ mu_f, float scale_f, int tile_w,
                                                       float *__restrict__ tile_c, float *__restrict__ tile_rho)
 {
-    __shared__ float csum[32];
-    __shared__ unsigned int rbits, ybits;
-    __shared__ int cnt;
-    const int64_t p = (int64_t)blockIdx.x * tile_w + threadIdx.x;
+    __shared__ float csum[2][32];
+    __shared__ unsigned int rbits[2], ybits;
+    __shared__ int cnt[2];
+    const int64_t p0 = (int64_t)blockIdx.x * tile_w;
+    const int64_t p = p0 + threadIdx.x;
     const bool valid = threadIdx.x < tile_w && p < N;
-    if (threadIdx.x < 32) csum[threadIdx.x] = 0.0f;
+    const int h = (valid && group && group[p] != group[p0]) ? 1 : 0;
+    if (threadIdx.x < 64) (&csum[0][0])[threadIdx.x] = 0.0f;
     if (threadIdx.x == 0) {
-        rbits = 0u;
+        rbits[0] = rbits[1] = 0u;
         ybits = 0u;
-        cnt = 0;
+        cnt[0] = cnt[1] = 0;
     }
     __syncthreads();
     float y[32];
@@ -422,11 +429,11 @@ __global__ void __launch_bounds__(128) k_tile_spheres(const float *__restrict__ 
             const float x = X[(int64_t)pos2row[p] * d + k];
             y[k] = (x - (mu_f ? mu_f[k] : 0.0f)) * scale_f;
             ny = fmaf(y[k], y[k], ny);
-            atomicAdd(&csum[k], y[k]);
+            atomicAdd(&csum[h][k], y[k]);
         }
     }
     if (valid) {
-        atomicAdd(&cnt, 1);
+        atomicAdd(&cnt[h], 1);
         atomicMax(&ybits, __float_as_uint(sqrtf(ny)));
     }
     __syncthreads();
@@ -434,21 +441,84 @@ __global__ void __launch_bounds__(128) k_tile_spheres(const float *__restrict__ 
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
         if (k < d) {
-            const float e = y[k] - csum[k] / (float)(cnt > 0 ? cnt : 1);
+            const float e = y[k] - csum[h][k] / (float)(cnt[h] > 0 ? cnt[h] : 1);
             dd = fmaf(e, e, dd);
         }
     }
-    if (valid) atomicMax(&rbits, __float_as_uint(sqrtf(dd)));
+    if (valid) atomicMax(&rbits[h], __float_as_uint(sqrtf(dd)));
     __syncthreads();
-    if (threadIdx.x < d) tile_c[(int64_t)blockIdx.x * d + threadIdx.x] = csum[threadIdx.x] / (float)(cnt > 0 ? cnt : 1);
-    if (threadIdx.x == 0) tile_rho[blockIdx.x] = sphere_slack(__uint_as_float(rbits), __uint_as_float(ybits));
+    for (int q = threadIdx.x; q < 2 * d; q += blockDim.x) {
+        const int hh = q / d, k = q - hh * d;
+        tile_c[((int64_t)blockIdx.x * 2 + hh) * d + k] = csum[hh][k] / (float)(cnt[hh] > 0 ? cnt[hh] : 1);
+    }
+    if (threadIdx.x < 2)
+        tile_rho[blockIdx.x * 2 + threadIdx.x] =
+            cnt[threadIdx.x] > 0 ? sphere_slack(__uint_as_float(rbits[threadIdx.x]), __uint_as_float(ybits)) : -1.0f;
 }
 
-cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const float *mu_f,
-                                float scale_f, int tile_w, float *tile_c, float *tile_rho, cudaStream_t s)
+cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const uint32_t *group,
+                                const float *mu_f, float scale_f, int tile_w, float *tile_c, float *tile_rho,
+                                cudaStream_t s)
 {
     const int64_t nt = (N + tile_w - 1) / tile_w;
-    k_tile_spheres<<<(unsigned)nt, 128, 0, s>>>(X, N, d, pos2row, mu_f, scale_f, tile_w, tile_c, tile_rho);
+    k_tile_spheres<<<(unsigned)nt, 128, 0, s>>>(X, N, d, pos2row, group, mu_f, scale_f, tile_w, tile_c, tile_rho);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+// One block of 64 threads per block of 32 tiles (thread = one of the tiles' two
+// spheres): centre = mean of the non-empty sphere centres, radius = the largest
+// |c - centre| + rho over them, enlarged by sphere_slack: a sphere holding all of them.
+__global__ void __launch_bounds__(64) k_block_spheres(const float *__restrict__ tile_c,
+                                                     const float *__restrict__ tile_rho, int64_t ntiles, int d,
+                                                     float *__restrict__ blk_c, float *__restrict__ blk_rho)
+{
+    __shared__ float csum[32];
+    __shared__ unsigned int rbits, ybits;
+    __shared__ int cnt;
+    const int64_t sp = (int64_t)blockIdx.x * 64 + threadIdx.x;   // sphere index: tile * 2 + part
+    const bool valid = sp < ntiles * 2 && tile_rho[sp] >= 0.0f;
+    if (threadIdx.x < 32) csum[threadIdx.x] = 0.0f;
+    if (threadIdx.x == 0) {
+        rbits = 0u;
+        ybits = 0u;
+        cnt = 0;
+    }
+    __syncthreads();
+    float c[32];
+    float nc = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        c[k] = (valid && k < d) ? tile_c[sp * d + k] : 0.0f;
+        nc = fmaf(c[k], c[k], nc);
+        if (valid && k < d) atomicAdd(&csum[k], c[k]);
+    }
+    const float rho = valid ? tile_rho[sp] : 0.0f;
+    if (valid) {
+        atomicAdd(&cnt, 1);
+        atomicMax(&ybits, __float_as_uint(__fadd_ru(sqrtf(nc), rho)));
+    }
+    __syncthreads();
+    if (valid) {
+        float dd = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (k < d) {
+                const float e = c[k] - csum[k] / (float)cnt;
+                dd = fmaf(e, e, dd);
+            }
+        atomicMax(&rbits, __float_as_uint(__fadd_ru(sqrtf(dd), rho)));
+    }
+    __syncthreads();
+    if (threadIdx.x < d) blk_c[(int64_t)blockIdx.x * d + threadIdx.x] = csum[threadIdx.x] / (float)(cnt > 0 ? cnt : 1);
+    if (threadIdx.x == 0) blk_rho[blockIdx.x] = cnt > 0 ? sphere_slack(__uint_as_float(rbits), __uint_as_float(ybits)) : -1.0f;
+}
+
+cudaError_t launch_block_spheres(const float *tile_c, const float *tile_rho, int64_t ntiles, int d, float *blk_c,
+                                 float *blk_rho, cudaStream_t s)
+{
+    const int64_t nb = (ntiles + 31) / 32;
+    k_block_spheres<<<(unsigned)nb, 64, 0, s>>>(tile_c, tile_rho, ntiles, d, blk_c, blk_rho);
     count_launches(1);
     return cudaGetLastError();
 }

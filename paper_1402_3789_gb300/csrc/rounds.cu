@@ -116,6 +116,12 @@ __global__ void k_best_d(RoundState st)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= st.N || st.row_state[i] != 1) return;
     atomicMin(&st.best_D[st.comp[i]], st.row_D[i]);
+    // the same pair leaves the other endpoint's component too: its D bounds that
+    // component's minimum from above
+    const unsigned long long ab = st.row_ab[i];
+    const uint32_t lo = (uint32_t)(ab >> 32), hi = (uint32_t)ab;
+    const uint32_t j = lo == (uint32_t)i ? hi : lo;
+    atomicMin(&st.comp_bound[st.comp[j]], st.row_D[i]);
 }
 
 __global__ void k_best_ab(RoundState st)
@@ -155,6 +161,19 @@ __global__ void k_flag(RoundState st)
         }
     }
     st.flag_pos[p] = f;
+}
+
+// A flagged row whose lower bound already exceeds a known outgoing D of its component
+// cannot hold the component's minimum: it is not rescanned.
+__global__ void k_flag_filter(RoundState st)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= st.N) return;
+    const uint32_t p = st.row2pos[i];
+    if (!st.flag_pos[p]) return;
+    const double lb = __longlong_as_double((long long)st.row_D[i]);
+    const double B = __longlong_as_double((long long)st.comp_bound[st.comp[i]]);
+    if (lb > B) st.flag_pos[p] = 0;
 }
 
 // Rescan rows in increasing position (so that a row tile of a rescan is spatially
@@ -211,7 +230,7 @@ __global__ void __launch_bounds__(kCompact) k_compact_scatter(RoundState st)
         const unsigned long long bd = st.best_D[c];
         double B = bd == kMaxKey ? INFINITY : __longlong_as_double((long long)bd);
         B = fmin(B, __longlong_as_double((long long)st.comp_bound[c]));
-        st.row_B[i] = B;
+        st.row_B[i] = B * st.overscan;
     }
 }
 
@@ -261,7 +280,38 @@ __global__ void k_relabel(RoundState st)
     st.comp[i] = st.parent[st.comp[i]];
 }
 
+// One warp per column tile: the component of each position, and the tile's common one.
+__global__ void k_position_comps(const RoundState st, int tile_w, uint32_t *__restrict__ comp_pos,
+                                 uint32_t *__restrict__ tile_comp, int64_t ntiles)
+{
+    const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= ntiles) return;
+    uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+    for (int q = lane; q < tile_w; q += 32) {
+        const int64_t p = t * tile_w + q;
+        if (p >= st.N) break;
+        const uint32_t c = st.comp[st.pos2row[p]];
+        comp_pos[p] = c;
+        lo = min(lo, c);
+        hi = max(hi, c);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) tile_comp[t] = lo == hi ? lo : kInvalid;
+}
+
 }  // namespace
+
+cudaError_t launch_position_comps(const RoundState &st, int tile_w, uint32_t *comp_pos, uint32_t *tile_comp,
+                                  cudaStream_t s)
+{
+    const int64_t ntiles = (st.N + tile_w - 1) / tile_w;
+    k_position_comps<<<(unsigned)((ntiles * 32 + kThreads - 1) / kThreads), kThreads, 0, s>>>(st, tile_w, comp_pos,
+                                                                                                tile_comp, ntiles);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_round_init(RoundState &st, cudaStream_t s)
 {
@@ -292,11 +342,12 @@ cudaError_t launch_component_min(RoundState &st, cudaStream_t s)
 cudaError_t launch_flag_rescans(RoundState &st, cudaStream_t s)
 {
     k_flag<<<grid_for(st.N), kThreads, 0, s>>>(st);
+    k_flag_filter<<<grid_for(st.N), kThreads, 0, s>>>(st);
     const int64_t nb = (st.N + kCompact - 1) / kCompact;
     k_compact_count<<<(unsigned)nb, kCompact, 0, s>>>(st);
     k_compact_prefix<<<1, 32, 0, s>>>(st, nb);
     k_compact_scatter<<<(unsigned)nb, kCompact, 0, s>>>(st);
-    count_launches(4);
+    count_launches(5);
     return cudaGetLastError();
 }
 

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     for (int r = 0; r < 2; ++r) {
         valid[r] = slot[r] < a.nslots;
         row[r] = valid[r] ? (a.rows ? a.rows[slot[r]] : (uint32_t)slot[r]) : 0u;   // position
-        crow[r] = (valid[r] && a.comp) ? a.comp[a.pos2row[row[r]]] : 0u;
+        crow[r] = (valid[r] && a.comp) ? a.comp_pos[row[r]] : 0u;
         const float *xr = a.Xs + (int64_t)row[r] * a.dp;
 #pragma unroll
         for (int k = 0; k < D; ++k) x[r][k] = k < a.dp ? xr[k] : 0.0f;
@@ -75,19 +75,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     // operand rows hold a.dp floats; the tile keeps DP >= a.dp per column (rest zero)
     if (a.dp < DP)
         for (int q = t; q < 2 * kTile * DP; q += kThreads) (&sy[0][0])[q] = 0.0f;
-    // Tile pruning: bounding sphere of this CTA's rows (the operands are the raw rows),
-    // and the block's largest row threshold after each tile.
-    __shared__ float cR[32], wthr[kThreads / 32], blk_thr;
-    __shared__ unsigned int rho_bits, ymax_bits;
-    __shared__ int nvalid;
-    if (t < 32) cR[t] = 0.0f;
+    // Tile pruning: bounding spheres of this CTA's rows (the operands are the raw rows)
+    // in two parts, the rows of the first landmark group and the rest, and each part's
+    // largest row threshold after each tile.
+    __shared__ float cR[2][32], wthr[2][kThreads / 32], blk_thr[2];
+    __shared__ unsigned int rho_bits[2], ymax_bits, cmin, cmax;
+    __shared__ int nvalid[2];
+    if (t < 64) (&cR[0][0])[t] = 0.0f;
     if (t == 0) {
-        rho_bits = 0u;
+        rho_bits[0] = rho_bits[1] = 0u;
         ymax_bits = 0u;
-        nvalid = 0;
-        blk_thr = INFINITY;
+        nvalid[0] = nvalid[1] = 0;
+        blk_thr[0] = blk_thr[1] = INFINITY;
+        cmin = 0xFFFFFFFFu;
+        cmax = 0u;
+    }
+    int part[2] = {0, 0};
+    if (a.prune) {
+        const uint32_t g0 = a.group[a.rows ? a.rows[(int64_t)blockIdx.x * kRowTile] : (uint32_t)(blockIdx.x * kRowTile)];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) part[r] = (valid[r] && a.group[row[r]] != g0) ? 1 : 0;
     }
     __syncthreads();
+    if (a.comp) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (valid[r]) {
+                atomicMin(&cmin, crow[r]);
+                atomicMax(&cmax, crow[r]);
+            }
+    }
     if (a.prune) {
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -96,9 +113,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 ny = fmaf(x[r][k], x[r][k], ny);
-                atomicAdd(&cR[k], x[r][k]);
+                atomicAdd(&cR[part[r]][k], x[r][k]);
             }
-            atomicAdd(&nvalid, 1);
+            atomicAdd(&nvalid[part[r]], 1);
             atomicMax(&ymax_bits, __float_as_uint(sqrtf(ny)));
         }
         __syncthreads();
@@ -108,38 +125,61 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
             float dd = 0.0f;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                const float e = x[r][k] - cR[k] / (float)nvalid;
+                const float e = x[r][k] - cR[part[r]][k] / (float)nvalid[part[r]];
                 dd = fmaf(e, e, dd);
             }
-            atomicMax(&rho_bits, __float_as_uint(sqrtf(dd)));
+            atomicMax(&rho_bits[part[r]], __float_as_uint(sqrtf(dd)));
         }
         __syncthreads();
-        if (t < D) cR[t] /= (float)(nvalid > 0 ? nvalid : 1);
+        if (t < 64 && (t & 31) < D) cR[t >> 5][t & 31] /= (float)(nvalid[t >> 5] > 0 ? nvalid[t >> 5] : 1);
     }
     __syncthreads();
-    const float rhoR = sphere_slack(__uint_as_float(rho_bits), __uint_as_float(ymax_bits));
+    float rhoR[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        rhoR[h] = nvalid[h] > 0 ? sphere_slack(__uint_as_float(rho_bits[h]), __uint_as_float(ymax_bits)) : -1.0f;
     // First kept tile at or after `from`.  Every thread takes the same decision; the lower
     // bounds of kThreads consecutive tiles are computed together (one per thread) into
     // lb_s when the scan leaves the current batch.
+    // A masked sweep whose rows all lie in one component skips that component's tiles.
     __shared__ float lb_s[kThreads];
+    __shared__ uint8_t own_s[kThreads];
+    const uint32_t rcomp = (a.comp && cmin == cmax) ? cmin : kInvalid;
     int64_t lb_base = -(int64_t)kThreads;
+    __shared__ float lb_s2[kThreads];
     auto next_kept = [&](int64_t from) -> int64_t {
-        if (!a.prune) return from;
-        const float thr = blk_thr;
+        if (!a.prune && rcomp == kInvalid) return from;
+        const float thr0 = blk_thr[0], thr1 = blk_thr[1];
         for (int64_t q = from; q < ntiles; ++q) {
             if (q >= lb_base + kThreads) {
                 __syncthreads();   // the previous batch is no longer read
                 lb_base = q;
-                float lb = -INFINITY;
+                float lb[2] = {-INFINITY, -INFINITY};
+                uint8_t own = 0;
                 if (q + t < ntiles) {
                     const int64_t ct = tile_col(q + t) / kTile;
-                    lb = tile_lower_bound(cR, rhoR, a.tile_c + ct * a.d, a.tile_rho[ct], a.d, 0.0f, a.lb_eps,
-                                          a.lb_gamma);
+                    own = rcomp != kInvalid && a.tile_comp[ct] == rcomp;
+                    if (a.prune && !own) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            lb[h] = INFINITY;
+                            if (rhoR[h] >= 0.0f)
+                                for (int hc = 0; hc < 2; ++hc) {
+                                    const float rc = a.tile_rho[ct * 2 + hc];
+                                    if (rc >= 0.0f)
+                                        lb[h] = fminf(lb[h], tile_lower_bound(cR[h], rhoR[h], a.tile_c + (ct * 2 + hc) * a.d,
+                                                                              rc, a.d, 0.0f, a.lb_eps, a.lb_gamma));
+                                }
+                        }
+                    }
                 }
-                lb_s[t] = lb;
+                lb_s[t] = lb[0];
+                lb_s2[t] = lb[1];
+                own_s[t] = own;
                 __syncthreads();
             }
-            if (!(lb_s[q - lb_base] > thr)) return q;
+            const int e = (int)(q - lb_base);
+            if (!own_s[e] && (!(lb_s[e] > thr0) || !(lb_s2[e] > thr1))) return q;
         }
         return ntiles;
     };
@@ -156,9 +196,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
         }
     };
 
+    uint32_t tcomp = kInvalid;   // component of the current column tile (kInvalid: mixed)
     auto consider = [&](int r, float v, uint32_t j) {
         if ((int64_t)j >= a.N || j == row[r]) return;
-        if (a.comp && a.comp[a.pos2row[j]] == crow[r]) return;
+        if (a.comp && (tcomp != kInvalid ? tcomp == crow[r] : a.comp_pos[j] == crow[r])) return;
         if (COLLECT) {
             if (!(v <= cthr[r])) return;
             const uint32_t p = atomicAdd(&a.coll_cnt[slot[r]], 1u);
@@ -170,16 +211,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     };
 
     // the block's largest row threshold, for the tile decisions of every thread
+    // (an empty part keeps -inf: its lower bound never keeps a tile)
     auto publish = [&](float th0, float th1) {
-        float wt = fmaxf(th0, th1);
+        float wt[2] = {-INFINITY, -INFINITY};
+        wt[part[0]] = th0;
+        wt[part[1]] = fmaxf(wt[part[1]], th1);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wt = fmaxf(wt, __shfl_xor_sync(0xffffffffu, wt, o));
-        if ((t & 31) == 0) wthr[t >> 5] = wt;
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wt[h] = fmaxf(wt[h], __shfl_xor_sync(0xffffffffu, wt[h], o));
+            if ((t & 31) == 0) wthr[h][t >> 5] = wt[h];
+        }
         __syncthreads();
-        if (t == 0) {
-            float m = wthr[0];
-            for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, wthr[w]);
-            blk_thr = m;
+        if (t < 2) {
+            float m = wthr[t][0];
+            for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, wthr[t][w]);
+            blk_thr[t] = m;
         }
         __syncthreads();
     };
@@ -217,7 +264,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
         const int n = (int)(a.N - j0 < kTile ? a.N - j0 : kTile);
         float th0 = COLLECT ? cthr[0] : sel[0].thr;
         float th1 = COLLECT ? cthr[1] : sel[1].thr;
-        for (int c = 0; c < n; c += 2) {
+        tcomp = a.comp ? a.tile_comp[tile_col(tile) / kTile] : kInvalid;
+        // rows of the tile's own component have nothing eligible in it
+        const bool own0 = !valid[0] || (a.comp && tcomp != kInvalid && tcomp == crow[0]);
+        const bool own1 = !valid[1] || (a.comp && tcomp != kInvalid && tcomp == crow[1]);
+        for (int c = (own0 && own1) ? n : 0; c < n; c += 2) {
             const float4 *ya = reinterpret_cast<const float4 *>(ys + c * DP);
             const float4 *yb = reinterpret_cast<const float4 *>(ys + (c + 1) * DP);
             float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;

@@ -28,6 +28,7 @@ constexpr int kThreadsTc = (kEpiWarps + 2) * 32;
 constexpr int kMmaWarp = 8;
 constexpr int kProdWarp = 9;
 constexpr int kBN = 128;          // columns per B tile
+constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere per block)
 constexpr int kMaxStages = 8;
 constexpr int kBandWide = 64;   // band slots per row for one-term BF16 (a wide band)
 constexpr int kStageStride = 36;   // floats per thread in the hit-staging area (16-byte rows, no bank conflicts)
@@ -189,13 +190,18 @@ struct __align__(8) TcShared {
     int abort_flag;
     int ring_tile[kMaxStages];   // column tile in each B stage (-1: end of the sequence)
     int acc_tile[2];             // column tile in each TMEM buffer (-1: end)
+    unsigned int ring_mask[kMaxStages];   // epilogue warps that need the tile in each stage
+    unsigned int acc_mask[2];             // ... and in each TMEM buffer
     float warp_thr[kEpiWarps];   // largest row threshold of each epilogue warp
-    float cR[32];                // row tile sphere: centre ...
-    unsigned int rho_bits, ymax_bits;   // ... radius and largest |y| (float bits)
-    int nvalid;
+    float cR[2][32];             // row tile spheres (part 0: the first landmark group of the
+    unsigned int rho_bits[2];    // tile's rows, part 1: the rest): centres, radii,
+    unsigned int ymax_bits;      // largest |y| (float bits) and row counts
+    int nvalid[2];
+    unsigned int warps_in[2];    // epilogue warps holding rows of each part (bit masks)
     int npub;                    // epilogue warps that have published a threshold
+    unsigned int cmin, cmax;     // smallest and largest component among the tile's rows
 };
-constexpr int kShBytes = 512;
+constexpr int kShBytes = 640;
 static_assert(sizeof(TcShared) <= kShBytes, "shared control block");
 
 // Shared-memory stages of the B ring that fit next to the other regions.
@@ -229,14 +235,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     // Column tiles in the order of the operands, starting at this row tile's own place
     // and wrapping around: near neighbours come first, so thresholds fall early.  Split
     // s takes the s-th range of that cyclic order.
+    // Column tiles are taken in blocks of kBlkTiles consecutive tiles (a block has a
+    // bounding sphere of its own); blocks in cyclic order starting at this row tile's own
+    // block; split s takes the s-th range of that order.
     const int ntile_all = (int)((a.N + kBN - 1) / kBN);
+    const int nblk_all = (ntile_all + kBlkTiles - 1) / kBlkTiles;
     const int tile0 = (int)((a.rows ? a.rows[slot0] : (uint32_t)slot0) / kBN);
-    const int tps = (int)(a.cols_per_split / kBN);
-    const int t_begin = split * tps;
-    const int t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
-    const int ntiles = t_end > t_begin ? t_end - t_begin : 0;
-    const int start = (tile0 + t_begin) % ntile_all;
-    auto col_tile = [&](int t) -> int { return start + t >= ntile_all ? start + t - ntile_all : start + t; };
+    const int bps = (nblk_all + a.splits - 1) / a.splits;
+    const int b_begin = split * bps;
+    const int b_end = b_begin + bps < nblk_all ? b_begin + bps : nblk_all;
+    const int nblk = b_end > b_begin ? b_end - b_begin : 0;
+    const int bstart = (tile0 / kBlkTiles + b_begin) % nblk_all;
+    auto blk_at = [&](int u) -> int { return bstart + u >= nblk_all ? bstart + u - nblk_all : bstart + u; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -250,11 +260,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         mbar_init(&sh->drain, 1);
         sh->abort_flag = 0;
         for (int w = 0; w < kEpiWarps; ++w) sh->warp_thr[w] = INFINITY;
-        for (int k = 0; k < 32; ++k) sh->cR[k] = 0.0f;
-        sh->rho_bits = 0u;
+        for (int k = 0; k < 32; ++k) sh->cR[0][k] = sh->cR[1][k] = 0.0f;
+        sh->rho_bits[0] = sh->rho_bits[1] = 0u;
         sh->ymax_bits = 0u;
-        sh->nvalid = 0;
+        sh->nvalid[0] = sh->nvalid[1] = 0;
+        sh->warps_in[0] = sh->warps_in[1] = 0u;
         sh->npub = 0;
+        sh->cmin = 0xFFFFFFFFu;
+        sh->cmax = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
@@ -270,6 +283,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     // of the tile's rows (centre = mean of y, radius = largest distance to it).
     int myrow_slot = -1;
     uint32_t myrow = 0, mycomp = 0;
+    int part = 0;   // sphere part of this thread's row
     float yv[32];
     if (warp < kEpiWarps) {
         const int r = (warp >> 2) * 128 + (warp & 3) * 32 + lane;   // row within the tile
@@ -279,7 +293,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         if (slot < a.nslots) {
             myrow_slot = r;
             myrow = a.rows ? a.rows[slot] : (uint32_t)slot;   // position
-            mycomp = a.comp ? a.comp[a.pos2row[myrow]] : 0u;
+            mycomp = a.comp ? a.comp_pos[myrow] : 0u;
+            if (a.comp) {
+                atomicMin(&sh->cmin, mycomp);
+                atomicMax(&sh->cmax, mycomp);
+            }
             const uint4 *src = reinterpret_cast<const uint4 *>(a.XA);
             for (int c = 0; c < chunks; ++c)
                 dst[((r >> 3) * chunks + c) * 8 + (r & 7)] = src[(((int64_t)myrow >> 3) * chunks + c) * 8 + (myrow & 7)];
@@ -288,6 +306,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (a.prune && myrow_slot >= 0) {
+            const uint32_t g0 = a.group[a.rows ? a.rows[slot0] : (uint32_t)slot0];
+            part = a.group[myrow] != g0 ? 1 : 0;
             const float *xr = a.X + (int64_t)a.pos2row[myrow] * a.d;
             float ny = 0.0f;
 #pragma unroll
@@ -296,11 +316,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 if (k < a.d) {
                     yv[k] = (xr[k] - (a.mu_f ? a.mu_f[k] : 0.0f)) * a.scale_f;
                     ny = fmaf(yv[k], yv[k], ny);
-                    atomicAdd(&sh->cR[k], yv[k]);
+                    atomicAdd(&sh->cR[part][k], yv[k]);
                 }
             }
-            atomicAdd(&sh->nvalid, 1);
+            atomicAdd(&sh->nvalid[part], 1);
             atomicMax(&sh->ymax_bits, __float_as_uint(sqrtf(ny)));
+        }
+        const unsigned int in0 = __ballot_sync(0xffffffffu, myrow_slot >= 0 && part == 0);
+        const unsigned int in1 = __ballot_sync(0xffffffffu, myrow_slot >= 0 && part == 1);
+        if (lane == 0) {
+            if (in0) atomicOr(&sh->warps_in[0], 1u << warp);
+            if (in1) atomicOr(&sh->warps_in[1], 1u << warp);
         }
     }
     __syncthreads();
@@ -309,15 +335,18 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
 #pragma unroll
         for (int k = 0; k < 32; ++k)
             if (k < a.d) {
-                const float e = yv[k] - sh->cR[k] / (float)sh->nvalid;
+                const float e = yv[k] - sh->cR[part][k] / (float)sh->nvalid[part];
                 dd = fmaf(e, e, dd);
             }
-        atomicMax(&sh->rho_bits, __float_as_uint(sqrtf(dd)));
+        atomicMax(&sh->rho_bits[part], __float_as_uint(sqrtf(dd)));
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (a.prune && threadIdx.x < 32 && threadIdx.x < a.d) sh->cR[threadIdx.x] /= (float)(sh->nvalid > 0 ? sh->nvalid : 1);
+    if (a.prune && threadIdx.x < 64 && (threadIdx.x & 31) < a.d) {
+        const int h = threadIdx.x >> 5;
+        sh->cR[h][threadIdx.x & 31] /= (float)(sh->nvalid[h] > 0 ? sh->nvalid[h] : 1);
+    }
     __syncthreads();
     const uint32_t tmem = sh->tmem_base;
     volatile int *abort_flag = &sh->abort_flag;
@@ -327,11 +356,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         // skipped when the lower bound of its candidate values exceeds every row's
         // threshold (the epilogue's published maxima, possibly stale = larger = safe).
         // The kept tiles' numbers travel with the stages; -1 ends the sequence.
-        const float rhoR = sphere_slack(__uint_as_float(sh->rho_bits), __uint_as_float(sh->ymax_bits));
+        float rhoR[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            rhoR[h] = sh->nvalid[h] > 0 ? sphere_slack(__uint_as_float(sh->rho_bits[h]), __uint_as_float(sh->ymax_bits))
+                                        : -1.0f;
+        const unsigned int win0 = sh->warps_in[0], win1 = sh->warps_in[1];
         int issued = 0, skipped = 0;
         bool ok_all = true;
-        // stage the column tile ct (-1: the end marker) into the next slot of the ring
-        auto issue = [&](int ct) -> bool {
+        // stage the column tile ct (-1: the end marker) into the next slot of the ring,
+        // with the epilogue warps that need it
+        auto issue = [&](int ct, unsigned int wmask) -> bool {
             const int s = issued % kStages;
             int ok = 1;
             if (lane == 0 && issued >= kStages)
@@ -343,6 +378,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             if (lane == 0) {
                 sh->ring_tile[s] = ct;
+                sh->ring_mask[s] = wmask;
                 if (ct < 0) {
                     mbar_arrive(&sh->full[s]);
                 } else {
@@ -354,49 +390,97 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             __syncwarp();
             return true;
         };
-        int t = 0;
-        if (a.prune) {
-            // Without thresholds known at the start, the first tile (the nearest columns)
-            // goes unconditionally and every later decision waits for the thresholds the
-            // epilogue learns from it: one tile of pipeline fill per CTA.  The wait is
-            // bounded; on time-out the decisions only get less selective.
-            if (!(COLLECT || a.row_B) && ntiles > 0) {
-                ok_all = issue(col_tile(0));
-                t = 1;
+        // tiles in this range (the last block of the operands may be short)
+        int range_tiles = nblk * kBlkTiles;
+        if (nblk > 0 && (nblk_all - 1 - bstart + nblk_all) % nblk_all < nblk)
+            range_tiles -= nblk_all * kBlkTiles - ntile_all;
+        // A masked sweep whose rows all lie in one component skips the column tiles of
+        // that component (every column there is ineligible).
+        const uint32_t rcomp = (a.comp && sh->cmin == sh->cmax) ? sh->cmin : kInvalid;
+        // Warps that need a sphere pair with lower bounds lb0 / lb1 for the row parts:
+        // those holding rows of a part whose bound does not exceed the warp's threshold
+        // (a snapshot: thresholds only fall, so a stale one only keeps more).
+        auto need_mask = [&](float lb0, float lb1) -> unsigned int {
+            unsigned int m = 0u;
+#pragma unroll
+            for (int w = 0; w < kEpiWarps; ++w) {
+                const float thr = ((volatile float *)sh->warp_thr)[w];
+                const bool need = (((win0 >> w) & 1u) && !(lb0 > thr)) || (((win1 >> w) & 1u) && !(lb1 > thr));
+                m |= need ? (1u << w) : 0u;
             }
-            if (ok_all && t < ntiles && lane == 0) {
+            return m;
+        };
+        auto part_bounds = [&](const float *cC, float rhoC, float &lb0, float &lb1) {
+            lb0 = rhoR[0] >= 0.0f && rhoC >= 0.0f
+                      ? tile_lower_bound(sh->cR[0], rhoR[0], cC, rhoC, a.d, a.lb_R2, a.lb_eps, a.lb_gamma)
+                      : INFINITY;
+            lb1 = rhoR[1] >= 0.0f && rhoC >= 0.0f
+                      ? tile_lower_bound(sh->cR[1], rhoR[1], cC, rhoC, a.d, a.lb_R2, a.lb_eps, a.lb_gamma)
+                      : INFINITY;
+        };
+        int first = -1;   // a tile issued before any decision
+        if (a.prune) {
+            // Without thresholds known at the start, one tile (this row tile's own, the
+            // nearest columns) goes unconditionally and every later decision waits for the
+            // thresholds the epilogue learns from it: one tile of pipeline fill per CTA.
+            // The wait is bounded; on time-out the decisions only get less selective.
+            if (!(COLLECT || a.row_B) && nblk > 0) {
+                first = split == 0 ? tile0 : blk_at(0) * kBlkTiles;
+                ok_all = issue(first, 0xFFu);
+            }
+            if (ok_all && nblk > 0 && lane == 0) {
                 const uint64_t t0 = global_ns();
                 while (((volatile int *)&sh->npub)[0] < kEpiWarps && !*abort_flag && global_ns() - t0 < kWaitNs)
                     __nanosleep(64);
             }
             __syncwarp();
         }
-        // 32 tiles per step: one lower bound per lane against one snapshot of the rows'
-        // largest threshold (thresholds only fall, so a stale one only keeps more)
-        while (ok_all && t < ntiles) {
-            const int n = ntiles - t < 32 ? ntiles - t : 32;
-            unsigned int keepm = n == 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
-            if (a.prune) {
-                float lb = -INFINITY;
+        // Level 1: 32 blocks per step, one per lane, against the blocks' spheres.  Level 2:
+        // in each block some warp needs, its tiles (one per lane) against the tiles' two
+        // spheres; the tile is skipped when no warp needs it.
+        for (int u0 = 0; ok_all && u0 < nblk; u0 += 32) {
+            const int nb = nblk - u0 < 32 ? nblk - u0 : 32;
+            bool bneed = lane < nb;
+            if (lane < nb && a.prune) {
+                const int cb = blk_at(u0 + lane);
+                float lb0, lb1;
+                part_bounds(a.blk_c + (int64_t)cb * a.d, a.blk_rho[cb], lb0, lb1);
+                bneed = need_mask(lb0, lb1) != 0u;
+            }
+            unsigned int bm = __ballot_sync(0xffffffffu, bneed);
+            while (ok_all && bm) {
+                const int q = __ffs(bm) - 1;
+                bm &= bm - 1u;
+                const int t0c = blk_at(u0 + q) * kBlkTiles;
+                const int n = ntile_all - t0c < kBlkTiles ? ntile_all - t0c : kBlkTiles;
+                unsigned int wmask = lane < n ? 0xFFu : 0u;
                 if (lane < n) {
-                    const int ct = col_tile(t + lane);
-                    lb = tile_lower_bound(sh->cR, rhoR, a.tile_c + (int64_t)ct * a.d, a.tile_rho[ct], a.d, a.lb_R2,
-                                          a.lb_eps, a.lb_gamma);
-                }
-                float thr = lane < kEpiWarps ? ((volatile float *)sh->warp_thr)[lane] : -INFINITY;
+                    const int ct = t0c + lane;
+                    if (ct == first || (rcomp != kInvalid && a.tile_comp[ct] == rcomp)) {
+                        wmask = 0u;
+                    } else if (a.prune) {
+                        float lb0 = INFINITY, lb1 = INFINITY;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) thr = fmaxf(thr, __shfl_xor_sync(0xffffffffu, thr, o));
-                keepm = __ballot_sync(0xffffffffu, lane < n && !(lb > thr));
-                skipped += n - __popc(keepm);
+                        for (int hc = 0; hc < 2; ++hc) {
+                            float l0, l1;
+                            part_bounds(a.tile_c + ((int64_t)ct * 2 + hc) * a.d, a.tile_rho[(int64_t)ct * 2 + hc], l0, l1);
+                            lb0 = fminf(lb0, l0);
+                            lb1 = fminf(lb1, l1);
+                        }
+                        wmask = need_mask(lb0, lb1);
+                    }
+                }
+                unsigned int keepm = __ballot_sync(0xffffffffu, wmask != 0u);
+                while (keepm) {
+                    const int e = __ffs(keepm) - 1;
+                    keepm &= keepm - 1u;
+                    const unsigned int m = __shfl_sync(0xffffffffu, wmask, e);
+                    if (!(ok_all = issue(t0c + e, m))) break;
+                }
             }
-            while (keepm) {
-                const int q = __ffs(keepm) - 1;
-                keepm &= keepm - 1u;
-                if (!(ok_all = issue(col_tile(t + q)))) break;
-            }
-            t += n;
         }
-        if (ok_all) issue(-1);
+        if (ok_all) issue(-1, 0u);
+        skipped = range_tiles - (issued > 0 ? issued - 1 : 0);
         if (lane == 0 && a.st_tiles) {
             atomicAdd(&a.st_tiles[0], (unsigned long long)skipped);
             atomicAdd(&a.st_tiles[1], (unsigned long long)(issued > 0 ? issued - 1 : 0));
@@ -436,6 +520,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             tc_fence_after();
             if (lane == 0) {
                 ((volatile int *)sh->acc_tile)[b] = tile;
+                ((volatile unsigned int *)sh->acc_mask)[b] = ((volatile unsigned int *)sh->ring_mask)[s];
                 if (tile >= 0) {
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
@@ -512,6 +597,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             return min(__vimin3_s32(l2a, l2b, l2c), l2d);
         };
         // The exact walk of one 32-column chunk through this thread's shared-memory row.
+        uint32_t tcomp = kInvalid;   // component of the current column tile (kInvalid: mixed)
         auto walk = [&](const uint32_t(&w)[32], int64_t jbase) {
             const float thr = COLLECT ? cthr : sel.thr;
             uint32_t mask = 0;
@@ -528,7 +614,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 const int64_t j = jbase + q;
                 if (!(val <= (COLLECT ? cthr : sel.thr))) continue;
                 if (j >= a.N || (uint32_t)j == myrow) continue;
-                if (a.comp && a.comp[a.pos2row[j]] == mycomp) continue;
+                if (a.comp && (tcomp != kInvalid ? tcomp == mycomp : a.comp_pos[j] == mycomp)) continue;
                 if (COLLECT) {
                     const int64_t sl = slot0 + myrow_slot;
                     const uint32_t p = atomicAdd(&a.coll_cnt[sl], 1u);
@@ -553,10 +639,29 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             mbar_try_wait(&sh->tfull[b], (q >> 1) & 1);
             tc_fence_after();
             int tile = 0;
-            if (lane == 0) tile = ((volatile int *)sh->acc_tile)[b];
+            unsigned int wmask = 0u;
+            if (lane == 0) {
+                tile = ((volatile int *)sh->acc_tile)[b];
+                wmask = ((volatile unsigned int *)sh->acc_mask)[b];
+            }
             tile = __shfl_sync(0xffffffffu, tile, 0);
+            wmask = __shfl_sync(0xffffffffu, wmask, 0);
             if (tile < 0) break;
             const int64_t col0 = (int64_t)tile * kBN;
+            if (!((wmask >> warp) & 1u)) {
+                // no row of this warp can have a candidate in the tile: release the buffer
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sh->tempty[b]);
+                continue;
+            }
+            if (a.comp) {
+                uint32_t tc = 0;
+                if (lane == 0) tc = a.tile_comp[tile];
+                tcomp = __shfl_sync(0xffffffffu, tc, 0);
+            }
+            // a row of the tile's own component has nothing eligible in it
+            const bool own = a.comp && tcomp != kInvalid && tcomp == mycomp;
             const uint32_t taddr = lane_base + (uint32_t)((b * 2 + half) * kBN);
 #pragma unroll 1
             for (int hh = 0; hh < kBN / 64; ++hh) {
@@ -573,7 +678,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 }
                 const int ithr = __float_as_int(COLLECT ? cthr : sel.thr);
                 const int m0 = imin32(va), m1 = imin32(vb);
-                if (min(m0, m1) <= ithr) {
+                if (!own && min(m0, m1) <= ithr) {
                     if (m0 <= ithr) walk(va, col0 + hh * 64);
                     if (m1 <= __float_as_int(COLLECT ? cthr : sel.thr)) walk(vb, col0 + hh * 64 + 32);
                 }
