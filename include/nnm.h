@@ -145,6 +145,9 @@ typedef struct {
     int64_t kernel_launches; /* kernels this library launched during the call      */
     int64_t tiles_skipped;   /* column tiles skipped by the bounding-sphere bound   */
     int64_t tiles_swept;     /* column tiles evaluated                              */
+    int64_t full_sweep_pairs_computed; /* (row, column) pairs in the tiles the full-matrix
+                                          sweep launch evaluated (256 rows x tile width
+                                          per tile): the work the launch did            */
 } nnm_stats;
 
 /* nnm_create -- "main module" ("Objectives of the main module"): validate the data

@@ -456,6 +456,11 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);
         c->stats.sweep_ms_per_launch_full = ms;
         c->stats.full_sweep_pairs = c->N * (c->N - 1);
+        // the first sweep of the call: the tile counter holds this launch's tiles
+        unsigned long long tiles = 0;
+        NNM_CUDA(c, cudaMemcpyAsync(&tiles, &c->dstat[14], sizeof tiles, cudaMemcpyDeviceToHost, c->stream));
+        NNM_CUDA(c, cudaStreamSynchronize(c->stream));
+        c->stats.full_sweep_pairs_computed = (int64_t)tiles * kRowTile * c->tile_w;
     }
     if (is_tensor(c)) NNM_TRY(check_sweep_error(c));
 
@@ -779,7 +784,9 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     st.cache_exh = c->cache_exh;
     st.row_B = c->row_B;
     st.comp_bound = c->comp_bound;
-    st.overscan = getenv("NNM_OVERSCAN") ? atof(getenv("NNM_OVERSCAN")) : 1.0;
+    // a rescan reaches a little beyond the bound it needs, so that the next rounds'
+    // (similar, slightly larger) bounds are often covered by its cache already
+    st.overscan = 1.25;
     st.X = c->X;
     st.d = c->d;
     st.row_D = c->row_D;

@@ -57,7 +57,7 @@ class nnm_stats(ctypes.Structure):
                 ("sweep_ms_per_launch_full", ctypes.c_double), ("full_sweep_pairs", ctypes.c_int64),
                 ("k_pad", ctypes.c_int32), ("cache_k", ctypes.c_int32), ("scale", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("tiles_skipped", ctypes.c_int64),
-                ("tiles_swept", ctypes.c_int64)]
+                ("tiles_swept", ctypes.c_int64), ("full_sweep_pairs_computed", ctypes.c_int64)]
 
 
 # every symbol include/nnm.h declares
