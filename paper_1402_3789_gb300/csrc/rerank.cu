@@ -44,15 +44,24 @@ __device__ double threshold(const Margin &m, uint32_t i, float vk)
     return ((U + rr) * (U + rr) + eps) * grow;
 }
 
+// Selections compare keys as integers: the bits of a non-negative double (or float)
+// order like the value, and the FP64 pipe, slow on this GPU, is kept for the distances.
+constexpr long long kInfD = 0x7FF0000000000000LL;   // bits of +inf (double)
+constexpr long long kInfF = 0x7F800000LL;           // bits of +inf (float)
+constexpr long long kNone = kInfF + 1;              // a float-key slot without a candidate
+constexpr long long kTaken = 1LL << 62;             // mark of an extracted float key
+
+__device__ __forceinline__ long long dkey(double x) { return __double_as_longlong(x); }
+
 struct Best {
-    double D;
+    long long key;
     uint32_t j;
     int e;
 };
 
-__device__ __forceinline__ bool less_dj(double D1, uint32_t j1, double D2, uint32_t j2)
+__device__ __forceinline__ bool less_kj(long long k1, uint32_t j1, long long k2, uint32_t j2)
 {
-    return D1 < D2 || (D1 == D2 && j1 < j2);
+    return k1 < k2 || (k1 == k2 && j1 < j2);
 }
 
 __device__ __forceinline__ Best warp_min(Best b)
@@ -60,12 +69,37 @@ __device__ __forceinline__ Best warp_min(Best b)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         Best c;
-        c.D = __shfl_xor_sync(0xffffffffu, b.D, o);
+        c.key = __shfl_xor_sync(0xffffffffu, b.key, o);
         c.j = __shfl_xor_sync(0xffffffffu, b.j, o);
         c.e = __shfl_xor_sync(0xffffffffu, b.e, o);
-        if (less_dj(c.D, c.j, b.D, b.j)) b = c;
+        if (less_kj(c.key, c.j, b.key, b.j)) b = c;
     }
     return b;
+}
+
+// k-th smallest of n float keys held as integers in kk (entries >= lim are ignored;
+// ties by position).  Extracted entries are marked and restored afterwards.  Returns
+// the value (+inf if fewer than k) and the number found.
+__device__ float kth_float(long long *kk, int n, int k, int *found)
+{
+    const int lane = threadIdx.x & 31;
+    int taken = 0;
+    long long vk = kInfF;
+    for (int m = 0; m < k; ++m) {
+        Best b = {kInfF, kInvalid, -1};
+        for (int e = lane; e < n; e += 32)
+            if (kk[e] < kInfF && less_kj(kk[e], (uint32_t)e, b.key, b.j)) b = {kk[e], (uint32_t)e, e};
+        b = warp_min(b);
+        if (b.e < 0) break;
+        vk = b.key;
+        ++taken;
+        if (lane == 0) kk[b.e] |= kTaken;
+        __syncwarp();
+    }
+    for (int e = lane; e < n; e += 32) kk[e] &= ~kTaken;
+    __syncwarp();
+    *found = taken;
+    return __int_as_float((int)vk);
 }
 
 // Pick the k smallest (D, j) of n entries held in (wD, wj) -- consumed entries get
@@ -76,13 +110,15 @@ __device__ void select_topk(double *wD, uint32_t *wj, int n, int k, uint32_t i, 
     const int lane = threadIdx.x & 31;
     int cnt = 0;
     for (int m = 0; m < k; ++m) {
-        Best b = {INFINITY, kInvalid, -1};
-        for (int e = lane; e < n; e += 32)
-            if (wD[e] < INFINITY && less_dj(wD[e], wj[e], b.D, b.j)) b = {wD[e], wj[e], e};
+        Best b = {kInfD, kInvalid, -1};
+        for (int e = lane; e < n; e += 32) {
+            const long long kd = dkey(wD[e]);
+            if (kd < kInfD && less_kj(kd, wj[e], b.key, b.j)) b = {kd, wj[e], e};
+        }
         b = warp_min(b);
         if (lane == 0) {
             res_j[(int64_t)i * k + m] = b.j;
-            res_D[(int64_t)i * k + m] = b.D;
+            res_D[(int64_t)i * k + m] = __longlong_as_double(b.key);
         }
         if (b.e < 0) continue;
         ++cnt;
@@ -103,8 +139,8 @@ __device__ __forceinline__ float fp32_D(const float *__restrict__ xi, const floa
     return s;
 }
 
-// Exact distances of the candidates in wD (entries < inf) of one row, cheapest first:
-// with refine, every candidate first gets its FP32 direct value s; from the k-th
+// Exact distances of the candidates in wD (entries 0, others +inf) of one row, cheapest
+// first: with refine, every candidate first gets its FP32 direct value s; from the k-th
 // smallest s the FP32 bound T32 (as for the FP32 sweep) keeps only the candidates that
 // can still be among the exact k nearest, and only those get the binary64 distance.
 // On return wD[e] = D (binary64) or +inf.  Returns the number of binary64 evaluations.
@@ -112,38 +148,29 @@ __device__ int exact_distances(const float *xi, const float *X, int d, double *w
                                const Margin &m, bool refine)
 {
     const int lane = threadIdx.x & 31;
-    double T32 = INFINITY;
+    long long *kk = reinterpret_cast<long long *>(wD);
+    long long lim = kInfD;   // entries with key <= lim (and not +inf) get the exact distance
     if (refine) {
+        // float keys of s in place of the marks (+inf keys for non-candidates)
         for (int e = lane; e < n; e += 32)
-            if (wD[e] < INFINITY) wD[e] = (double)fp32_D(xi, X + (int64_t)wj[e] * d, d);
+            kk[e] = kk[e] < kInfD ? (long long)__float_as_int(fp32_D(xi, X + (int64_t)wj[e] * d, d)) : kNone;
         __syncwarp();
-        // k-th smallest s: extracted entries are marked by w -> -1 - w and restored after
         int taken = 0;
-        double vk = INFINITY;
-        for (int mth = 0; mth < k; ++mth) {
-            Best b = {INFINITY, kInvalid, -1};
-            for (int e = lane; e < n; e += 32)
-                if (wD[e] >= 0.0 && wD[e] < INFINITY && less_dj(wD[e], (uint32_t)e, b.D, b.j)) b = {wD[e], (uint32_t)e, e};
-            b = warp_min(b);
-            if (b.e < 0) break;
-            vk = b.D;
-            ++taken;
-            if (lane == 0) wD[b.e] = -1.0 - wD[b.e];
-            __syncwarp();
-        }
-        for (int e = lane; e < n; e += 32)
-            if (wD[e] < 0.0) wD[e] = -1.0 - wD[e];
-        __syncwarp();
+        const float vk = kth_float(kk, n, k, &taken);
+        float t32 = INFINITY;
         if (taken == k) {
             const double grow = 1.0 + 1e-12;
-            const double us = (vk + m.alpha32) / (1.0 - m.gamma32) * grow;
-            T32 = (us * (1.0 + m.gamma32) + m.alpha32) * grow;
+            const double us = ((double)vk + m.alpha32) / (1.0 - m.gamma32) * grow;
+            t32 = __double2float_ru((us * (1.0 + m.gamma32) + m.alpha32) * grow);
         }
+        lim = (long long)__float_as_int(t32);   // +inf: every candidate
+        for (int e = lane; e < n; e += 32) kk[e] = kk[e] <= lim ? 0LL : kInfD;   // back to marks
+        __syncwarp();
     }
     int nd = 0;
     for (int e = lane; e < n; e += 32) {
         double D = INFINITY;
-        if (wD[e] < INFINITY && wD[e] <= T32) {
+        if (kk[e] == 0LL) {
             D = canon_D(xi, X + (int64_t)wj[e] * d, d);
             ++nd;
         }
@@ -171,33 +198,25 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     const uint32_t i = a.pos2row[ipos];
     const float *vin = a.in_v + q * n_ent;
     const uint32_t *jin = a.in_j + q * n_ent;
+    long long *kk = reinterpret_cast<long long *>(wD);
     for (int e = lane; e < n_ent; e += 32) {
         const uint32_t j = jin[e];   // a position; from here on original row indices
         const float v = vin[e];
         wv[e] = v;
         wj[e] = j != kInvalid ? a.pos2row[j] : kInvalid;
-        wD[e] = j != kInvalid ? (double)v : INFINITY;
+        // candidate values are >= 0 except the tensor path's small negative rounding:
+        // the key is clamped at +0 (a larger k-th value only keeps more)
+        kk[e] = j != kInvalid ? (long long)__float_as_int(v > 0.0f ? v : 0.0f) : kNone;
     }
     const bool ovf = lane < a.splits && a.in_ovf[q * a.splits + lane];
     __syncwarp();
-    // k-th smallest value over all records (extraction on a scratch copy)
+    // k-th smallest value over all records
     int taken = 0;
-    double vk = INFINITY;
-    for (int m = 0; m < a.k; ++m) {
-        Best b = {INFINITY, kInvalid, -1};
-        for (int e = lane; e < n_ent; e += 32)
-            if (wD[e] < INFINITY && less_dj(wD[e], (uint32_t)e, b.D, b.j)) b = {wD[e], (uint32_t)e, e};
-        b = warp_min(b);
-        if (b.e < 0) break;
-        vk = b.D;
-        ++taken;
-        if (lane == 0) wD[b.e] = INFINITY;
-        __syncwarp();
-    }
+    const float vk = kth_float(kk, n_ent, a.k, &taken);
     // a bounded row needs only columns with D <= B: their candidate values are at most
     // the threshold of the value B (in candidate units)
     const double B = a.row_B ? a.row_B[i] : INFINITY;
-    double T = threshold(a.m, i, taken < a.k ? INFINITY : (float)vk);
+    double T = threshold(a.m, i, taken < a.k ? INFINITY : vk);
     if (B < INFINITY) T = fmin(T, threshold(a.m, i, __double2float_ru(B / a.m.inv_scale2)));
     const bool any_ovf = __any_sync(0xffffffffu, ovf);
     if (lane == 0) {
@@ -206,20 +225,24 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     }
     if (any_ovf) return;
     const float *xi = a.X + (int64_t)i * a.d;
-    for (int e = lane; e < n_ent; e += 32) wD[e] = (wj[e] != kInvalid && (double)wv[e] <= T) ? 0.0 : INFINITY;
+    const float Tf = __double2float_ru(T);   // >= T: keeps a superset
+    for (int e = lane; e < n_ent; e += 32) wD[e] = (wj[e] != kInvalid && wv[e] <= Tf) ? 0.0 : INFINITY;
     __syncwarp();
     const int nc = exact_distances(xi, a.X, a.d, wD, wj, n_ent, a.k, a.m, a.m.tensor != 0);
     if (B < INFINITY) {
+        const long long kb = dkey(B);
         for (int e = lane; e < n_ent; e += 32)
-            if (wD[e] > B) wD[e] = INFINITY;
+            if (dkey(wD[e]) > kb) wD[e] = INFINITY;
         __syncwarp();
     }
-    double emax_abs = 0.0, emax_rel = 0.0;
+    double emax_abs = 0.0;
+    float emax_rel = 0.0f;
     for (int e = lane; e < n_ent; e += 32) {
-        if (wD[e] < INFINITY) {
+        const long long kd = dkey(wD[e]);
+        if (kd < kInfD) {
             const double err = fabs((double)wv[e] * a.m.inv_scale2 - wD[e]);
             emax_abs = fmax(emax_abs, err);
-            if (wD[e] > 0.0) emax_rel = fmax(emax_rel, err / wD[e]);
+            if (kd > 0) emax_rel = fmaxf(emax_rel, (float)err / (float)wD[e]);
         }
     }
     int n_out;
@@ -227,7 +250,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         emax_abs = fmax(emax_abs, __shfl_xor_sync(0xffffffffu, emax_abs, o));
-        emax_rel = fmax(emax_rel, __shfl_xor_sync(0xffffffffu, emax_rel, o));
+        emax_rel = fmaxf(emax_rel, __shfl_xor_sync(0xffffffffu, emax_rel, o));
     }
     if (lane == 0) {
         if (a.res_n) a.res_n[i] = (uint8_t)n_out;
@@ -235,7 +258,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
         // among the candidates
         if (a.res_exh) a.res_exh[i] = (uint8_t)(n_out < a.k && !(B < INFINITY));
         atomic_max_nonneg(a.st_max_abs, emax_abs);
-        atomic_max_nonneg(a.st_max_rel, emax_rel);
+        atomic_max_nonneg(a.st_max_rel, (double)emax_rel);
         if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nc);
         if (a.st_max_cand) atomicMax(a.st_max_cand, (unsigned long long)nc);
     }
@@ -272,7 +295,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
     const double B = a.row_B ? a.row_B[i] : INFINITY;
     if (B < INFINITY)
         for (uint32_t e = lane; e < cnt; e += 32)
-            if (wD[e] > B) wD[e] = INFINITY;
+            if (dkey(wD[e]) > dkey(B)) wD[e] = INFINITY;
     __threadfence_block();
     int n_out;
     select_topk(wD, wj, (int)cnt, a.k, i, a.res_j, a.res_D, &n_out);
