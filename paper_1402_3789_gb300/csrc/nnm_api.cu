@@ -75,7 +75,8 @@ struct nnm_ctx {
     float *heavy_thr = nullptr, *heavy_thr2 = nullptr;
     size_t heavy_cap = 0;        // rows
     // cache and rounds
-    int kc = 0;
+    int kc = 0;   // cache width (neighbours kept per row by the first sweep)
+    int kr = 0;   // neighbours kept by a rescan (<= kc)
     uint32_t *cache_j = nullptr;
     double *cache_D = nullptr;
     uint8_t *cache_n = nullptr, *cache_exh = nullptr;
@@ -334,7 +335,7 @@ constexpr size_t kCollectBytes = (size_t)4 << 30;   // collect buffers (uint32 +
 // their exact count.
 nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n, int64_t cap, int k,
                    const uint32_t *comp, uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh,
-                   const double *row_B)
+                   const double *row_B, int res_stride)
 {
     cudaStream_t s = c->stream;
     NNM_TRY(ensure_heavy(c, (size_t)n));
@@ -386,6 +387,7 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
             ra.res_D = res_D;
             ra.res_n = res_n;
             ra.res_exh = res_exh;
+            ra.res_stride = res_stride;
             ra.row_B = row_B;
             ra.retry_flag = &c->derr[1];
             ra.heavy_flag = c->heavy_flag;
@@ -421,9 +423,10 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
 // res_j/res_D [row][k] (and res_n / res_exh if given).
 nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, const uint32_t *comp,
                    uint32_t *res_j, double *res_D, uint8_t *res_n, uint8_t *res_exh, bool full,
-                   const double *row_B = nullptr)
+                   const double *row_B = nullptr, int res_stride = 0)
 {
     if (nslots <= 0) return NNM_OK;
+    if (res_stride < k) res_stride = k;
     const int S = choose_splits(c, nslots);
     const int64_t cps = round_up((c->N + S - 1) / S, 128);
     const int splits = (int)((c->N + cps - 1) / cps);
@@ -484,6 +487,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
         fa.res_D = res_D;
         fa.res_n = res_n;
         fa.res_exh = res_exh;
+        fa.res_stride = res_stride;
         fa.row_B = row_B;
         fa.ovf_flag = c->ovf_flag;
         fa.ovf_thr = c->ovf_thr_slot;
@@ -504,7 +508,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
     // run again with room for all of them.  Batches keep the buffers within kCollectBytes.
     c->stats.rows_overflowed += novf;
     NNM_TRY(collect(c, c->ovf_row, c->ovf_thr, novf, is_tensor(c) ? 1024 : 256, k, comp, res_j, res_D, res_n,
-                    res_exh, row_B));
+                    res_exh, row_B, res_stride));
     return NNM_OK;
 }
 
@@ -851,8 +855,8 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
         if (nres > 0) {
             c->stats.rows_rescanned += nres;
             NNM_CUDA(c, launch_position_comps(st, c->tile_w, c->comp_pos, c->tile_comp, s));
-            NNM_TRY(run_knn(c, c->list_pos, nres, c->kc, c->comp, c->cache_j, c->cache_D, c->cache_n, c->cache_exh,
-                            false, c->row_B));
+            NNM_TRY(run_knn(c, c->list_pos, nres, c->kr, c->comp, c->cache_j, c->cache_D, c->cache_n, c->cache_exh,
+                            false, c->row_B, c->kc));
             Phase ph(c, &c->stats.ms_rounds);
             NNM_CUDA(c, launch_resolve(st, c->list, nres, s));
             NNM_CUDA(c, launch_component_min(st, s));
@@ -943,6 +947,7 @@ nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metri
     c->stream = (cudaStream_t)cuda_stream;
     c->kc = c->opt.cache_k > 0 ? c->opt.cache_k : (precision == NNM_PREC_BF16_RERANK ? 2 : 8);
     if (c->kc > N - 1) c->kc = N > 1 ? (int)(N - 1) : 1;
+    c->kr = c->kc;
     cudaGetDevice(&c->device);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);

@@ -22,6 +22,11 @@ constexpr int kRowTile = 256;     // rows per sweep CTA (both candidate paths)
 constexpr int kMaxSplits = 32;    // column ranges per row tile
 constexpr uint64_t kMaxKey = 0xFFFFFFFFFFFFFFFFull;
 
+// State of a row's neighbour cache after a scan for its k nearest eligible columns:
+constexpr uint8_t kCacheFull = 0;      // k found: every other eligible column has a larger key
+constexpr uint8_t kCacheAll = 1;       // fewer found: they are every eligible column
+constexpr uint8_t kCacheBounded = 2;   // fewer found: every other eligible column has D > the row's bound
+
 // The exact squared distance of Eq. (1): D = ((t_0 + t_1) + ...) + t_{d-1},
 // t_k = e_k * e_k, e_k = x_ik - x_jk, each operation binary64 round-to-nearest, no
 // contraction (the same value for (i, j) and (j, i)).
@@ -183,7 +188,8 @@ struct FinalizeArgs {
     uint32_t *res_j;           // [N][k]
     double *res_D;             // [N][k]
     uint8_t *res_n;            // valid results per row (nullable)
-    uint8_t *res_exh;          // 1: the results hold every eligible column (nullable)
+    uint8_t *res_exh;          // cache state per row (kCache*, nullable)
+    int res_stride;            // row stride of res_j / res_D (>= k)
     const double *row_B;       // per original row: keep only D <= row_B (nullptr: no bound)
     // incomplete rows -> collect pass (compacted afterwards in slot order, so that the
     // collect pass keeps the spatial order of the rows)
@@ -215,6 +221,7 @@ struct CollectRerankArgs {
     double *res_D;
     uint8_t *res_n;
     uint8_t *res_exh;
+    int res_stride;
     const double *row_B;       // as in FinalizeArgs
     int *retry_flag;           // set when a slot collected more than cap
     uint8_t *heavy_flag;       // [heavy_base + p] 1: slot p collected more than cap

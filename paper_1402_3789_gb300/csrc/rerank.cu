@@ -104,7 +104,7 @@ __device__ float kth_float(long long *kk, int n, int k, int *found)
 
 // Pick the k smallest (D, j) of n entries held in (wD, wj) -- consumed entries get
 // D = +inf -- and write them to the row's result slots.
-__device__ void select_topk(double *wD, uint32_t *wj, int n, int k, uint32_t i, uint32_t *res_j,
+__device__ void select_topk(double *wD, uint32_t *wj, int n, int k, int stride, uint32_t i, uint32_t *res_j,
                            double *res_D, int *n_out)
 {
     const int lane = threadIdx.x & 31;
@@ -117,8 +117,8 @@ __device__ void select_topk(double *wD, uint32_t *wj, int n, int k, uint32_t i, 
         }
         b = warp_min(b);
         if (lane == 0) {
-            res_j[(int64_t)i * k + m] = b.j;
-            res_D[(int64_t)i * k + m] = __longlong_as_double(b.key);
+            res_j[(int64_t)i * stride + m] = b.j;
+            res_D[(int64_t)i * stride + m] = __longlong_as_double(b.key);
         }
         if (b.e < 0) continue;
         ++cnt;
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
         }
     }
     int n_out;
-    select_topk(wD, wj, n_ent, a.k, i, a.res_j, a.res_D, &n_out);
+    select_topk(wD, wj, n_ent, a.k, a.res_stride, i, a.res_j, a.res_D, &n_out);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         emax_abs = fmax(emax_abs, __shfl_xor_sync(0xffffffffu, emax_abs, o));
@@ -254,9 +254,9 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     }
     if (lane == 0) {
         if (a.res_n) a.res_n[i] = (uint8_t)n_out;
-        // fewer than k results from an unbounded row means every eligible column was
-        // among the candidates
-        if (a.res_exh) a.res_exh[i] = (uint8_t)(n_out < a.k && !(B < INFINITY));
+        // fewer than k results: every eligible column (unbounded row), or every eligible
+        // column with D <= B (bounded row), is among them
+        if (a.res_exh) a.res_exh[i] = n_out == a.k ? kCacheFull : (B < INFINITY ? kCacheBounded : kCacheAll);
         atomic_max_nonneg(a.st_max_abs, emax_abs);
         atomic_max_nonneg(a.st_max_rel, (double)emax_rel);
         if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nc);
@@ -298,10 +298,10 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
             if (dkey(wD[e]) > dkey(B)) wD[e] = INFINITY;
     __threadfence_block();
     int n_out;
-    select_topk(wD, wj, (int)cnt, a.k, i, a.res_j, a.res_D, &n_out);
+    select_topk(wD, wj, (int)cnt, a.k, a.res_stride, i, a.res_j, a.res_D, &n_out);
     if (lane == 0) {
         if (a.res_n) a.res_n[i] = (uint8_t)n_out;
-        if (a.res_exh) a.res_exh[i] = (uint8_t)((int)cnt < a.k && !(B < INFINITY));
+        if (a.res_exh) a.res_exh[i] = n_out == a.k ? kCacheFull : (B < INFINITY ? kCacheBounded : kCacheAll);
         if (a.st_pairs) atomicAdd(a.st_pairs, (unsigned long long)nd);
         if (a.st_max_cand) atomicMax(a.st_max_cand, (unsigned long long)cnt);
     }

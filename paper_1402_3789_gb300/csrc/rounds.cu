@@ -80,11 +80,12 @@ __global__ void k_resolve(RoundState st, const uint32_t *__restrict__ rows, int6
             return;
         }
     }
-    if (st.cache_exh[i]) {
+    const uint8_t cs = st.cache_exh[i];
+    if (cs == kCacheAll || (n == 0 && cs == kCacheFull)) {
         st.row_state[i] = 0;   // every eligible column was cached: none is outside
         return;
     }
-    if (n < st.k) {
+    if (cs == kCacheBounded) {
         // bounded scan: every column not cached has D > row_B
         const double B = st.row_B[i];
         if (!(B < INFINITY)) {

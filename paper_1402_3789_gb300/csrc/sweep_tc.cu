@@ -80,6 +80,22 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_fl
     }
 }
 
+// Whole-warp bounded wait: every lane polls and the warp decides together, so that no
+// lane waits alone while the others stall at the next warp-wide operation.  Every lane
+// observes the completed phase itself (acquire).
+__device__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        if (it == 0) t0 = global_ns();
+        if ((it & 15) == 15) {
+            const int give_up = __shfl_sync(0xffffffffu, (int)(*abort_flag != 0 || global_ns() - t0 > kWaitNs), 0);
+            if (give_up) return false;
+        }
+    }
+}
+
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
@@ -626,17 +642,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         };
         for (int q = 0;; ++q) {
             const int b = q & 1;
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait(&sh->tfull[b], (q >> 1) & 1, abort_flag);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
+            if (!mbar_wait_warp(&sh->tfull[b], (q >> 1) & 1, abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
-            // every lane acquires the completed phase itself before reading TMEM (the phase
-            // cannot move on before this warp releases the buffer, so this returns at once);
             // the tile number comes from lane 0 so that the whole warp decides alike
-            mbar_try_wait(&sh->tfull[b], (q >> 1) & 1);
             tc_fence_after();
             int tile = 0;
             unsigned int wmask = 0u;
