@@ -204,6 +204,33 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+KERNEL_SOURCES = ["paper_1402_3789_gb300/csrc/sweep_tc.cu", "paper_1402_3789_gb300/csrc/select.cuh",
+                  "paper_1402_3789_gb300/csrc/nnm_internal.cuh"]
+
+
+def captured_traffic(precision, N):
+    """DRAM bytes per launch of the sweep from a committed ncu capture (profiles/*_dram.md)
+    of this precision and N, if the kernel's sources are still the ones captured."""
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    sha = h.hexdigest()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*_dram.md")):
+        kv = {}
+        with open(path) as fh:
+            for ln in fh:
+                ln = ln.strip()
+                if ":" in ln and ln.split(":", 1)[0] in ("precision", "N", "kernel_sources_sha1", "dram_bytes_per_launch"):
+                    k, v = ln.split(":", 1)
+                    kv[k] = v.strip()
+        if kv.get("precision") == precision and kv.get("N") == str(N) and kv.get("kernel_sources_sha1") == sha:
+            return float(kv["dram_bytes_per_launch"]), os.path.basename(path)
+    return None, None
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -273,7 +300,10 @@ def run_ours(args, world, rank, local):
         peak = peaks.get("bf16_tflops_sustained", 1700.0)   # same rate for fp16 operands
         roof = {"bound": "tensor", "peak_source": f"bf16_tflops_sustained ({peak_kind})"}
     achieved = flops / (sweep_ms / 1e3) / 1e12
-    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+    traffic, traffic_src = captured_traffic(args.precision, N)
+    if traffic is not None:
+        roof["traffic_source"] = f"profiles/{traffic_src} (ncu, dram__bytes_read.sum + dram__bytes_write.sum)"
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                  "kernel": "k_sweep_tc" if args.precision != "fp32" else "k_sweep_fp32",
                  "algorithmic_flops_per_launch": flops, "flops_per_pair": per_pair,
                  "pairs_per_launch": sweep_pairs, "pairs_full_matrix": all_pairs,
@@ -347,11 +377,69 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+BATCHED = "nnm_batched512"
+
+
+def run_batched(args, world, rank):
+    """Many independent instances of uneven N and d, one create + cluster + destroy per
+    instance (one launch sequence each); every instance resident on the device first."""
+    import torch
+
+    from paper_1402_3789_gb300 import nnm
+    from paper_1402_3789_gb300.inputs import batched_instances
+
+    nnm.load_library()
+    inst = batched_instances()
+    Xs = [torch.from_numpy(x).cuda() for x in inst]
+    pairs = sum(x.shape[0] * (x.shape[0] - 1) / 2 for x in inst)
+    stream = torch.cuda.current_stream()
+
+    def step(precision):
+        sweep = 0.0
+        for Xd in Xs:
+            ctx = nnm.nnm_create(Xd, precision=precision)
+            try:
+                nnm.nnm_cluster(ctx, {})
+                sweep += nnm.nnm_get_stats(ctx)["ms_sweep"]
+            finally:
+                nnm.nnm_destroy(ctx)
+        return sweep
+
+    for _ in range(args.warmup):
+        step(args.precision)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sweeps = [step(args.precision) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world) / args.steps
+    line = {"metric": "G pair-distances/s, 512 independent dendrograms (one launch sequence per instance)",
+            "value": world * pairs / (ms / 1e3) / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"bf16": "bf16+f64", "bf16x3": "bf16x3+f64", "fp16": "f16+f64",
+                                          "fp32": "f32+f64"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": BATCHED, "instances": len(inst), "rows_total": sum(x.shape[0] for x in inst),
+                       "precision": args.precision, "parallelism": "replicas" if world > 1 else "single"},
+            "sweep_ms_per_step": statistics.mean(sweeps), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == BATCHED:
+        run_batched(args, world, rank)
     else:
         run_ours(args, world, rank, local)
     if world > 1:
