@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--compare", default="fp16,bf16,fp32", help="comma list of other precisions timed for one step each")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--ref-seconds", type=float, default=None, help="oracle seconds per step of --impl reference")
     return p.parse_args()
 
 
@@ -172,7 +173,7 @@ def run_reference(args, world, rank):
         return
     X = make(args.workload, n=args.n)
     N, d = X.shape
-    per_step = max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
+    per_step = args.ref_seconds if args.ref_seconds else max(2.0, min(20.0, 150.0 / max(args.steps + args.warmup, 1)))
     rates = []
     for s in range(args.warmup + args.steps):
         rate, R, dt, cores = oracle_pair_rate(X, per_step, seed=s)
