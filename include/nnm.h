@@ -166,6 +166,26 @@ nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metri
                       nnm_precision precision, void *cuda_stream, const nnm_options *options,
                       nnm_ctx **out);
 
+/* nnm_create_batched -- one context for many independent problems (instances) that share
+ * d: instance b is rows [offsets_host[b], offsets_host[b+1]) of X_dev.  Distances,
+ * neighbours and merges never cross instances: nnm_nearest gives each row its k nearest
+ * within its own instance; nnm_cluster gives the merge forest (one tree per instance,
+ * N - n_instances edges; nnm_get_tree returns it grouped by instance, each group in key
+ * order), applies the restrictions to each instance on its own (KL1 counts the clusters
+ * of that instance), returns the merges grouped by instance (each group in acceptance
+ * order) and labels over all rows.  Instances with fewer
+ * features are passed padded with zero columns: zero columns leave every distance and
+ * therefore every result unchanged.  The paper runs one problem per program start; this
+ * form serves many small problems in one pass of each kernel.
+ *   offsets_host  int64 [n_instances + 1] host memory, 0 = offsets[0] < ... <
+ *                 offsets[n_instances] = N < 2^31; read during the call only.
+ *   n_instances   1 .. 65535.
+ * Other arguments and errors as nnm_create; EINVAL also for bad offsets.  nnm_nearest
+ * requires k < rows of the smallest instance. */
+nnm_status nnm_create_batched(const float *X_dev, const int64_t *offsets_host, int64_t n_instances, int32_t d,
+                              nnm_metric metric, nnm_precision precision, void *cuda_stream,
+                              const nnm_options *options, nnm_ctx **out);
+
 /* nnm_nearest -- exact k nearest neighbours of every row (self excluded), in order
  * of (D, index): the per-row minima of the second and third parallel items of
  * "Overall idea of the algorithm" (all pairwise distances, minimum selection).

@@ -50,6 +50,14 @@ struct nnm_ctx {
     SelConst selc{};
     // spatial order of the operands (see prep.cu) and the column tiles' bounding spheres
     uint32_t *pos2row = nullptr, *row2pos = nullptr, *list_pos = nullptr, *group = nullptr;
+    // batched contexts: independent instances of contiguous rows (n_inst == 1: none)
+    int64_t n_inst = 1;
+    int64_t min_inst_rows = 0;
+    int64_t *inst_off = nullptr;   // device [n_inst + 1]; positions = rows of each instance
+    uint32_t *inst_pos = nullptr;  // device [N]: instance of each position (and row)
+    int64_t *ebeg = nullptr, *eend = nullptr;   // edge range of each instance in the tree
+    unsigned long long *inst_nm = nullptr;      // merges per instance (restriction walks)
+    nnm_merge *merges_tmp = nullptr;
     float *tile_c = nullptr, *tile_rho = nullptr, *mu_f = nullptr, *blk_c = nullptr, *blk_rho = nullptr;
     int tile_w = 0;
     float lb_R2 = 0.f, lb_eps = 0.f, lb_gamma = 0.f;
@@ -189,6 +197,7 @@ bool is_tensor(const nnm_ctx *c) { return c->prec != NNM_PREC_FP32; }
 // Column ranges per row tile: enough CTAs to fill the 152 SMs a few times.
 int choose_splits(const nnm_ctx *c, int64_t nslots)
 {
+    if (c->n_inst > 1) return 1;   // each row tile sweeps its own instance only
     if (c->opt.col_split > 0) return c->opt.col_split < kMaxSplits ? c->opt.col_split : kMaxSplits;
     const int64_t row_ctas = (nslots + kRowTile - 1) / kRowTile;
     const int64_t target = is_tensor(c) ? 152 * 4 : 152 * 2 * 4;
@@ -290,6 +299,8 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.tile_c = c->tile_c;
     a.tile_rho = c->tile_rho;
     a.group = c->group;
+    a.inst_pos = c->inst_pos;
+    a.inst_off = c->inst_off;
     a.blk_c = c->blk_c;
     a.blk_rho = c->blk_rho;
     a.mu_f = c->mu_f;
@@ -617,14 +628,14 @@ nnm_status prepare(nnm_ctx *c)
         cudaError_t e = launch_landmark_chain(c->X, c->N, c->d, S, crank, s);
         if (e == cudaSuccess) e = launch_nearest_ref(c->X, c->N, c->d, L, S, larg, ldist, s);
         if (e == cudaSuccess)
-            e = launch_spatial_keys(larg, ldist, L, crank, nullptr, nullptr, 0, nullptr, nullptr, nullptr, lkeys,
-                                    nullptr, 0, s);
+            e = launch_spatial_keys(larg, ldist, L, crank, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr,
+                                    lkeys, nullptr, 0, s);
         if (e == cudaSuccess) e = launch_sort_edges(lkeys, ltmp, L, s, &lsorted);
         if (e == cudaSuccess) e = launch_order_from_keys(lsorted, L, lpos, lrank, nullptr, s);
         if (e == cudaSuccess) e = launch_nearest_ref(c->X, c->N, c->d, c->N, L, rarg, rdist, s);
         if (e == cudaSuccess)
-            e = launch_spatial_keys(nullptr, nullptr, 0, nullptr, rarg, rdist, c->N, lrank, hist, tau, nullptr, keys, 1,
-                                    s);
+            e = launch_spatial_keys(nullptr, nullptr, 0, nullptr, rarg, rdist, c->N, lrank, c->inst_pos, hist, tau,
+                                    nullptr, keys, 1, s);
         if (e == cudaSuccess) e = launch_sort_edges(keys, tmp, c->N, s, &sorted);
         if (e == cudaSuccess) e = launch_order_from_keys(sorted, c->N, c->pos2row, c->row2pos, c->group, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -738,6 +749,12 @@ nnm_status ensure_rounds(nnm_ctx *c)
     NNM_TRY(dalloc(c, &c->row_B, (size_t)N));
     NNM_TRY(dalloc(c, &c->comp_bound, (size_t)N));
     NNM_TRY(dalloc(c, &c->comp_pos, (size_t)N));
+    if (c->n_inst > 1) {
+        NNM_TRY(dalloc(c, &c->ebeg, (size_t)c->n_inst));
+        NNM_TRY(dalloc(c, &c->eend, (size_t)c->n_inst));
+        NNM_TRY(dalloc(c, &c->inst_nm, (size_t)c->n_inst + 1));
+        NNM_TRY(dalloc(c, &c->merges_tmp, (size_t)N));
+    }
     NNM_TRY(dalloc(c, &c->tile_comp, (size_t)((N + c->tile_w - 1) / c->tile_w)));
     NNM_TRY(dalloc(c, &c->parent, (size_t)N));
     NNM_TRY(dalloc(c, &c->list, (size_t)N));
@@ -793,6 +810,7 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     st.overscan = 1.25;
     st.X = c->X;
     st.d = c->d;
+    st.inst_pos = c->inst_pos;
     st.row_D = c->row_D;
     st.row_ab = c->row_ab;
     st.row_state = c->row_state;
@@ -903,7 +921,11 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     c->n_tree = ne;
     {
         Phase ph(c, &c->stats.ms_sort);
-        NNM_CUDA(c, launch_sort_edges(c->edges, c->edges_tmp, c->n_tree, s, &c->tree));
+        // a batched context keeps each instance's edges together (then in key order)
+        NNM_CUDA(c, launch_sort_edges(c->edges, c->edges_tmp, c->n_tree, s, &c->tree,
+                                      c->n_inst > 1 ? c->inst_pos : nullptr));
+        if (c->n_inst > 1)
+            NNM_CUDA(c, launch_edge_ranges(c->tree, c->n_tree, c->inst_pos, c->n_inst, c->ebeg, c->eend, s));
     }
     return NNM_OK;
 }
@@ -926,8 +948,9 @@ const char *nnm_status_string(nnm_status s)
     return "unknown";
 }
 
-nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metric, nnm_precision precision,
-                      void *cuda_stream, const nnm_options *options, nnm_ctx **out)
+static nnm_status create_impl(const float *X_dev, int64_t N, int32_t d, const int64_t *offsets, int64_t n_inst,
+                              nnm_metric metric, nnm_precision precision, void *cuda_stream,
+                              const nnm_options *options, nnm_ctx **out)
 {
     if (!out) return NNM_EINVAL;
     *out = nullptr;
@@ -938,6 +961,14 @@ nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metri
         return NNM_EUNSUPPORTED;
     if (precision == NNM_PREC_BF16X3_RERANK && d > 30) return NNM_EUNSUPPORTED;
     if (options && (options->cache_k < 0 || options->cache_k > 16 || options->col_split < 0)) return NNM_EINVAL;
+    int64_t min_rows = N;
+    if (offsets) {
+        if (n_inst < 1 || n_inst > 65535 || offsets[0] != 0 || offsets[n_inst] != N) return NNM_EINVAL;
+        for (int64_t b = 0; b < n_inst; ++b) {
+            if (offsets[b + 1] <= offsets[b]) return NNM_EINVAL;
+            if (offsets[b + 1] - offsets[b] < min_rows) min_rows = offsets[b + 1] - offsets[b];
+        }
+    }
     nnm_ctx *c = new nnm_ctx();
     c->X = X_dev;
     c->N = N;
@@ -948,11 +979,22 @@ nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metri
     c->kc = c->opt.cache_k > 0 ? c->opt.cache_k : (precision == NNM_PREC_BF16_RERANK ? 2 : 8);
     if (c->kc > N - 1) c->kc = N > 1 ? (int)(N - 1) : 1;
     c->kr = c->kc;
+    c->min_inst_rows = min_rows;
     cudaGetDevice(&c->device);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
-    nnm_status st;
-    {
+    nnm_status st = NNM_OK;
+    if (offsets && n_inst > 1) {
+        c->n_inst = n_inst;
+        st = dalloc(c, &c->inst_off, (size_t)(n_inst + 1));
+        if (st == NNM_OK) st = dalloc(c, &c->inst_pos, (size_t)N);
+        if (st == NNM_OK &&
+            (cudaMemcpyAsync(c->inst_off, offsets, (size_t)(n_inst + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                             c->stream) != cudaSuccess ||
+             launch_instance_ids(c->inst_off, n_inst, N, c->inst_pos, c->stream) != cudaSuccess))
+            st = fail(c, NNM_ECUDA, "instance ids");
+    }
+    if (st == NNM_OK) {
         Phase ph(c, &c->stats.ms_prep);
         st = prepare(c);
     }
@@ -964,13 +1006,32 @@ nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metri
     return NNM_OK;
 }
 
+nnm_status nnm_create(const float *X_dev, int64_t N, int32_t d, nnm_metric metric, nnm_precision precision,
+                      void *cuda_stream, const nnm_options *options, nnm_ctx **out)
+{
+    return create_impl(X_dev, N, d, nullptr, 1, metric, precision, cuda_stream, options, out);
+}
+
+nnm_status nnm_create_batched(const float *X_dev, const int64_t *offsets_host, int64_t n_instances, int32_t d,
+                              nnm_metric metric, nnm_precision precision, void *cuda_stream,
+                              const nnm_options *options, nnm_ctx **out)
+{
+    if (!offsets_host || n_instances < 1) {
+        if (out) *out = nullptr;
+        return NNM_EINVAL;
+    }
+    return create_impl(X_dev, offsets_host[n_instances], d, offsets_host, n_instances, metric, precision,
+                       cuda_stream, options, out);
+}
+
 nnm_status nnm_nearest(nnm_ctx *c, int32_t k, uint32_t *idx_dev, double *D_dev)
 {
     if (!c) return NNM_EINVAL;
     c->err.clear();
     c->status = NNM_OK;
     if (!idx_dev || !D_dev) return fail(c, NNM_EINVAL, "null output buffer");
-    if (k < 1 || k > kMaxK || (int64_t)k >= c->N) return fail(c, NNM_EINVAL, "k=%d outside 1..min(16, N-1)", k);
+    if (k < 1 || k > kMaxK || (int64_t)k >= c->min_inst_rows)
+        return fail(c, NNM_EINVAL, "k=%d outside 1..min(16, rows of the smallest instance - 1)", k);
     reset_stats(c);
     {
         Phase total(c, &c->stats.ms_total);
@@ -1020,6 +1081,12 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
             ra.merges = merges_dev;
             ra.n_merges = &c->dstat[4];
             ra.err_flag = &c->derr[3];
+            ra.n_inst = c->n_inst;
+            ra.inst_off = c->inst_off;
+            ra.ebeg = c->ebeg;
+            ra.eend = c->eend;
+            ra.inst_nm = c->inst_nm;
+            ra.merges_tmp = c->merges_tmp;
             NNM_CUDA(c, launch_restrict(ra, c->stream));
         }
         {
@@ -1073,6 +1140,12 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->tile_c);
     dfree(c->tile_rho);
     dfree(c->group);
+    dfree(c->inst_off);
+    dfree(c->inst_pos);
+    dfree(c->ebeg);
+    dfree(c->eend);
+    dfree(c->inst_nm);
+    dfree(c->merges_tmp);
     dfree(c->blk_c);
     dfree(c->blk_rho);
     dfree(c->mu_f);

@@ -82,6 +82,8 @@ struct SweepArgs {
     // rows and columns are positions in the spatial order of the operands
     const uint32_t *rows;     // slot -> row position (nullptr: slot q is position q)
     int64_t nslots;
+    const uint32_t *inst_pos;   // batched contexts: instance of each position (nullptr:
+    const int64_t *inst_off;    // one instance); instance b = positions [inst_off[b], inst_off[b+1])
     const uint32_t *comp_pos;   // with comp: component of each position
     const uint32_t *tile_comp;  // with comp: component of each column tile of tile_w
                                 // positions when they all share one, else kInvalid
@@ -247,8 +249,11 @@ cudaError_t launch_nearest_ref(const float *X, int64_t N, int d, int64_t Q, int6
                                cudaStream_t s);
 cudaError_t launch_spatial_keys(const uint32_t *larg, const float *ldist, int64_t L, const uint32_t *crank,
                                 const uint32_t *rarg, const float *rdist, int64_t N, const uint32_t *lrank,
+                                const uint32_t *inst /* nullable: instance of each row, most significant */,
                                 unsigned int *hist, float *tau, nnm_edge *lkeys, nnm_edge *rkeys, int which,
                                 cudaStream_t s);
+// inst[p] = b for p in [off[b], off[b+1])
+cudaError_t launch_instance_ids(const int64_t *off, int64_t B, int64_t N, uint32_t *inst, cudaStream_t s);
 cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,
                                    uint32_t *group /* nullable: landmark group per position */, cudaStream_t s);
 // out[q] = map[in[q]]
@@ -302,6 +307,7 @@ struct RoundState {
     double overscan;               // rescan bound = overscan * the component's bound
     const float *X;                // [N][d] the rows (exact distances of the bound search)
     int d;
+    const uint32_t *inst_pos;      // batched contexts: instance of each position (nullable)
     unsigned long long *row_D;     // [N] key of the row's best outgoing candidate (D bits)
     unsigned long long *row_ab;    // [N] (min << 32) | max
     uint8_t *row_state;            // 0 none, 1 resolved, 2 unresolved (row_D/row_ab: bound)
@@ -335,7 +341,7 @@ cudaError_t launch_position_comps(const RoundState &st, int tile_w, uint32_t *co
 // Sort (K6), restriction walk (K7), labels (K8)
 // ---------------------------------------------------------------------------------
 cudaError_t launch_sort_edges(nnm_edge *e, nnm_edge *tmp, int64_t m, cudaStream_t s,
-                              nnm_edge **sorted_out);
+                              nnm_edge **sorted_out, const uint32_t *major = nullptr);
 
 struct RestrictArgs {
     const nnm_edge *edges;     // key-sorted tree edges
@@ -349,9 +355,21 @@ struct RestrictArgs {
     nnm_merge *merges;         // [N-1] out
     unsigned long long *n_merges; // device out
     int *err_flag;
+    // batched contexts: one walk per instance (CTA b), the edges sorted by (instance,
+    // key); instance b = rows [inst_off[b], inst_off[b+1]), edges [ebeg[b], eend[b]).
+    // Each walk writes its merges at merges_tmp[ebeg[b]..] and their count to inst_nm[b];
+    // launch_restrict then packs them into merges in instance order.
+    int64_t n_inst;
+    const int64_t *inst_off;
+    const int64_t *ebeg, *eend;
+    unsigned long long *inst_nm;   // [n_inst + 1] scratch
+    nnm_merge *merges_tmp;         // [m] scratch
 };
 
 cudaError_t launch_restrict(const RestrictArgs &a, cudaStream_t s);
+// ebeg[b], eend[b]: the edge range of each instance in edges sorted by (instance, key)
+cudaError_t launch_edge_ranges(const nnm_edge *edges, int64_t m, const uint32_t *inst_of_row, int64_t n_inst,
+                               int64_t *ebeg, int64_t *eend, cudaStream_t s);
 
 struct LabelArgs {
     int64_t N;

@@ -212,26 +212,43 @@ __global__ void k_landmark_keys(const uint32_t *__restrict__ arg, const float *_
     keys[m] = e;
 }
 
-// Sort keys of the rows: (isolated, rank of the landmark group, distance).
+// Sort keys of the rows: (instance, isolated, rank of the landmark group, distance), the
+// distance by its top 24 bits (an order-preserving truncation), in one exact double:
+// instance < 2^16, 1 + 12 bits, 24 bits.
 __global__ void k_row_keys(const uint32_t *__restrict__ arg, const float *__restrict__ dist, int64_t N,
-                           const uint32_t *__restrict__ lrank, const float *__restrict__ tau,
-                           nnm_edge *__restrict__ keys)
+                           const uint32_t *__restrict__ lrank, const uint32_t *__restrict__ inst,
+                           const float *__restrict__ tau, nnm_edge *__restrict__ keys)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float v = dist[i];
-    const double far = v > *tau ? 8192.0 : 0.0;   // above every group rank (< 4096)
+    const double far = v > *tau ? 4096.0 : 0.0;   // above every group rank (< 4096)
+    const double b = inst ? (double)inst[i] * 8192.0 : 0.0;
     nnm_edge e;
     e.a = (uint32_t)i;
     e.b = 0u;
-    e.D = (far + (double)lrank[arg[i]]) * 4294967296.0 + (double)__float_as_uint(v);   // exact: < 2^53
+    e.D = (b + far + (double)lrank[arg[i]]) * 16777216.0 + (double)(__float_as_uint(v) >> 8);   // exact: < 2^53
     keys[i] = e;
+}
+
+__global__ void k_instance_ids(const int64_t *__restrict__ off, int64_t B, int64_t N, uint32_t *__restrict__ inst)
+{
+    const int64_t b = blockIdx.x;
+    if (b >= B) return;
+    for (int64_t p = off[b] + threadIdx.x; p < off[b + 1] && p < N; p += blockDim.x) inst[p] = (uint32_t)b;
+}
+
+cudaError_t launch_instance_ids(const int64_t *off, int64_t B, int64_t N, uint32_t *inst, cudaStream_t s)
+{
+    k_instance_ids<<<(unsigned)B, 256, 0, s>>>(off, B, N, inst);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_spatial_keys(const uint32_t *larg, const float *ldist, int64_t L, const uint32_t *crank,
                                 const uint32_t *rarg, const float *rdist, int64_t N, const uint32_t *lrank,
-                                unsigned int *hist, float *tau, nnm_edge *lkeys, nnm_edge *rkeys, int which,
-                                cudaStream_t s)
+                                const uint32_t *inst, unsigned int *hist, float *tau, nnm_edge *lkeys,
+                                nnm_edge *rkeys, int which, cudaStream_t s)
 {
     if (which == 0) {
         k_landmark_keys<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(larg, ldist, L, crank, lkeys);
@@ -244,7 +261,7 @@ cudaError_t launch_spatial_keys(const uint32_t *larg, const float *ldist, int64_
     if (blocks > 152 * 4) blocks = 152 * 4;
     k_dist_hist<<<blocks, 256, 0, s>>>(rdist, N, hist);
     k_dist_tau<<<1, 32, 0, s>>>(hist, N, tau);
-    k_row_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rarg, rdist, N, lrank, tau, rkeys);
+    k_row_keys<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(rarg, rdist, N, lrank, inst, tau, rkeys);
     count_launches(3);
     return cudaGetLastError();
 }

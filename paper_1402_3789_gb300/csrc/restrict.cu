@@ -2,6 +2,7 @@
 //
 // The restrictions of "Problem statement" and "Problem settings" (maximum joining
 // distance, KL1..KL4) act on the merge sequence: the tree edges are walked in key order
+// (in a batched context: each instance's edges, one CTA per instance, in parallel)
 // with a union-find that tracks cluster sizes and the cluster count.  The walk is
 // sequential by definition (each decision reads sizes that earlier joins changed), so
 // it runs in one CTA over chunks of 2048 edges:
@@ -143,17 +144,25 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
     __shared__ uint32_t tot1, tot2;
     __shared__ int64_t m_adm, n_def, n_out;
     const int t = threadIdx.x;
+    // this walk's rows and edges: everything, or (batched) instance blockIdx.x
+    const bool batched = a.n_inst > 1;
+    const int64_t rlo = batched ? a.inst_off[blockIdx.x] : 0, rhi = batched ? a.inst_off[blockIdx.x + 1] : a.N;
+    const int64_t elo = batched ? a.ebeg[blockIdx.x] : 0, ehi = batched ? a.eend[blockIdx.x] : a.m;
+    const int64_t nrows = rhi - rlo;
+    const nnm_edge *edges = a.edges + elo;
+    nnm_merge *merges = batched ? a.merges_tmp + elo : a.merges;
+    uint32_t *deferred = a.deferred + elo;
 
-    for (int64_t i = t; i < a.N; i += kWalkThreads) {
+    for (int64_t i = rlo + t; i < rhi; i += kWalkThreads) {
         a.uf_parent[i] = (uint32_t)i;
         a.uf_size[i] = 1u;
     }
     if (t == 0) {
         // admissible prefix: the edges are key-sorted, so D <= cap^2 is a prefix
-        int64_t lo = 0, hi = a.m;
+        int64_t lo = 0, hi = ehi - elo;
         while (lo < hi) {
             int64_t mid = (lo + hi) >> 1;
-            if (a.edges[mid].D <= a.cap2) lo = mid + 1;
+            if (edges[mid].D <= a.cap2) lo = mid + 1;
             else hi = mid;
         }
         m_adm = lo;
@@ -172,8 +181,8 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
             const int n = (int)(total - c0 < kChunk ? total - c0 : kChunk);
             // 1. global roots
             for (int e = t; e < n; e += kWalkThreads) {
-                const int64_t ei = walk == 0 ? c0 + e : (int64_t)a.deferred[c0 + e];
-                const nnm_edge ed = a.edges[ei];
+                const int64_t ei = walk == 0 ? c0 + e : (int64_t)deferred[c0 + e];
+                const nnm_edge ed = edges[ei];
                 S.ra[e] = gfind(a.uf_parent, ed.a);
                 S.rb[e] = gfind(a.uf_parent, ed.b);
             }
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
                     }
                     if (a.kl2 > 0 && (sx > (uint64_t)a.kl2 || sy > (uint64_t)a.kl2)) continue;
                     if (a.kl3 > 0 && (uint64_t)sx + sy > (uint64_t)a.kl3) continue;
-                    if (a.kl1 > 0 && a.N - joined <= a.kl1) {
+                    if (a.kl1 > 0 && nrows - joined <= a.kl1) {
                         S.stop = 1;
                         continue;
                     }
@@ -251,18 +260,18 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
             }
             scan2_block(S, n, &tot1, &tot2);
             for (int e = t; e < n; e += kWalkThreads) {
-                const int64_t ei = walk == 0 ? c0 + e : (int64_t)a.deferred[c0 + e];
+                const int64_t ei = walk == 0 ? c0 + e : (int64_t)deferred[c0 + e];
                 if (S.dec[e] == 1) {
-                    const nnm_edge ed = a.edges[ei];
+                    const nnm_edge ed = edges[ei];
                     nnm_merge mg;
                     mg.a = ed.a;
                     mg.b = ed.b;
                     mg.D = ed.D;
                     mg.dist = sqrt(ed.D);
                     mg.new_size = S.newsize[e];
-                    a.merges[n_out + S.scan1[e]] = mg;
+                    merges[n_out + S.scan1[e]] = mg;
                 } else if (S.dec[e] == 2) {
-                    a.deferred[n_def + S.scan2[e]] = (uint32_t)ei;
+                    deferred[n_def + S.scan2[e]] = (uint32_t)ei;
                 }
             }
             __syncthreads();
@@ -273,7 +282,42 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
             __syncthreads();
         }
     }
-    if (t == 0) *a.n_merges = (unsigned long long)n_out;
+    if (t == 0) {
+        if (batched) a.inst_nm[blockIdx.x] = (unsigned long long)n_out;
+        else *a.n_merges = (unsigned long long)n_out;
+    }
+}
+
+// Batched walks: exclusive prefix of the per-instance merge counts (one thread), then
+// one block per instance copies its merges into place.
+__global__ void k_merge_offsets(unsigned long long *nm, int64_t n_inst, unsigned long long *total)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int64_t b = 0; b < n_inst; ++b) {
+        const unsigned long long v = nm[b];
+        nm[b] = run;
+        run += v;
+    }
+    nm[n_inst] = run;
+    *total = run;
+}
+
+__global__ void k_merge_pack(const RestrictArgs a)
+{
+    const int64_t b = blockIdx.x;
+    const unsigned long long o = a.inst_nm[b], n = a.inst_nm[b + 1] - o;
+    for (unsigned long long q = threadIdx.x; q < n; q += blockDim.x) a.merges[o + q] = a.merges_tmp[a.ebeg[b] + q];
+}
+
+__global__ void k_edge_ranges(const nnm_edge *__restrict__ e, int64_t m, const uint32_t *__restrict__ inst,
+                              int64_t *__restrict__ ebeg, int64_t *__restrict__ eend)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t b = inst[e[i].a];
+    if (i == 0 || inst[e[i - 1].a] != b) ebeg[b] = i;
+    if (i == m - 1 || inst[e[i + 1].a] != b) eend[b] = i + 1;
 }
 
 constexpr int kLabThreads = 256;
@@ -350,7 +394,24 @@ cudaError_t launch_restrict(const RestrictArgs &a, cudaStream_t s)
     const size_t smem = sizeof(WalkShared);
     cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_restrict<<<1, kWalkThreads, smem, s>>>(a);
+    const bool batched = a.n_inst > 1;
+    k_restrict<<<batched ? (unsigned)a.n_inst : 1u, kWalkThreads, smem, s>>>(a);
+    count_launches(1);
+    if (batched) {
+        k_merge_offsets<<<1, 32, 0, s>>>(a.inst_nm, a.n_inst, a.n_merges);
+        k_merge_pack<<<(unsigned)a.n_inst, 256, 0, s>>>(a);
+        count_launches(2);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_ranges(const nnm_edge *edges, int64_t m, const uint32_t *inst_of_row, int64_t n_inst,
+                               int64_t *ebeg, int64_t *eend, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(ebeg, 0, (size_t)n_inst * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(eend, 0, (size_t)n_inst * sizeof(int64_t), s);
+    if (e != cudaSuccess || m <= 0) return e;
+    k_edge_ranges<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(edges, m, inst_of_row, ebeg, eend);
     count_launches(1);
     return cudaGetLastError();
 }

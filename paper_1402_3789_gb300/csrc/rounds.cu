@@ -152,6 +152,7 @@ __global__ void k_flag(RoundState st)
                 for (int s = 1; s <= kNeighbourSearch; ++s) {
                     const int64_t q = (int64_t)p + side * s;
                     if (q < 0 || q >= st.N) break;
+                    if (st.inst_pos && st.inst_pos[q] != st.inst_pos[p]) break;   // another instance
                     const uint32_t j = st.pos2row[q];
                     if (st.comp[j] == c) continue;
                     const double D = canon_D(xi, st.X + (int64_t)j * st.d, st.d);

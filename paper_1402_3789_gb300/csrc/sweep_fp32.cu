@@ -58,10 +58,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
 
     // Column tiles in the order of the operands, starting at this row tile's own place and
     // wrapping around (near neighbours first); split s takes the s-th range of that order.
+    // In a batched context only the tiles of the row tile's instances, [rtb, rte).
     const int split = blockIdx.y;
-    const int64_t ntile_all = (a.N + kTile - 1) / kTile;
-    const int64_t tile0 = (int64_t)(a.rows ? a.rows[(int64_t)blockIdx.x * kRowTile] : (uint32_t)(blockIdx.x * kRowTile)) /
-                          kTile;
+    const int64_t slot_first = (int64_t)blockIdx.x * kRowTile;
+    const int64_t p_first = a.rows ? a.rows[slot_first] : slot_first;
+    int64_t rtb = 0, rte = (a.N + kTile - 1) / kTile;
+    if (a.inst_pos) {
+        const int64_t last = (slot_first + kRowTile < a.nslots ? slot_first + kRowTile : a.nslots) - 1;
+        const int64_t p_last = a.rows ? a.rows[last] : last;
+        rtb = a.inst_off[a.inst_pos[p_first]] / kTile;
+        rte = (a.inst_off[a.inst_pos[p_last] + 1] + kTile - 1) / kTile;
+    }
+    const int64_t ntile_all = rte - rtb;
+    const int64_t tile0 = p_first / kTile - rtb;
     const int64_t tps = a.cols_per_split / kTile;
     const int64_t t_begin = (int64_t)split * tps;
     const int64_t t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
@@ -69,8 +78,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     const int64_t start = (tile0 + t_begin) % ntile_all;
     auto tile_col = [&](int64_t tile) -> int64_t {
         const int64_t x = start + tile;
-        return (x >= ntile_all ? x - ntile_all : x) * kTile;
+        return (rtb + (x >= ntile_all ? x - ntile_all : x)) * kTile;
     };
+    // the columns of each row's instance (all columns when not batched)
+    int64_t ibeg[2] = {0, 0}, iend[2] = {a.N, a.N};
+    if (a.inst_pos) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (valid[r]) {
+                ibeg[r] = a.inst_off[a.inst_pos[row[r]]];
+                iend[r] = a.inst_off[a.inst_pos[row[r]] + 1];
+            }
+    }
 
     // operand rows hold a.dp floats; the tile keeps DP >= a.dp per column (rest zero)
     if (a.dp < DP)
@@ -199,6 +218,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     uint32_t tcomp = kInvalid;   // component of the current column tile (kInvalid: mixed)
     auto consider = [&](int r, float v, uint32_t j) {
         if ((int64_t)j >= a.N || j == row[r]) return;
+        if ((int64_t)j < ibeg[r] || (int64_t)j >= iend[r]) return;   // another instance
         if (a.comp && (tcomp != kInvalid ? tcomp == crow[r] : a.comp_pos[j] == crow[r])) return;
         if (COLLECT) {
             if (!(v <= cthr[r])) return;

@@ -248,21 +248,35 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
     const int64_t slot0 = (int64_t)blockIdx.x * kRowTile;
-    // Column tiles in the order of the operands, starting at this row tile's own place
-    // and wrapping around: near neighbours come first, so thresholds fall early.  Split
-    // s takes the s-th range of that cyclic order.
-    // Column tiles are taken in blocks of kBlkTiles consecutive tiles (a block has a
-    // bounding sphere of its own); blocks in cyclic order starting at this row tile's own
-    // block; split s takes the s-th range of that order.
+    // The column tiles this row tile may meet: all of them, or in a batched context the
+    // tiles of its rows' instances, [rtb, rte).  They are taken in blocks of kBlkTiles
+    // consecutive tiles (a block has a bounding sphere of its own), blocks in cyclic order
+    // starting at this row tile's own block (near neighbours first, so thresholds fall
+    // early); split s takes the s-th range of that order.
     const int ntile_all = (int)((a.N + kBN - 1) / kBN);
-    const int nblk_all = (ntile_all + kBlkTiles - 1) / kBlkTiles;
-    const int tile0 = (int)((a.rows ? a.rows[slot0] : (uint32_t)slot0) / kBN);
+    const int64_t p_first = a.rows ? a.rows[slot0] : slot0;
+    int rtb = 0, rte = ntile_all;
+    if (a.inst_pos) {
+        const int64_t last = (slot0 + kRowTile < a.nslots ? slot0 + kRowTile : a.nslots) - 1;
+        const int64_t p_last = a.rows ? a.rows[last] : last;
+        rtb = (int)(a.inst_off[a.inst_pos[p_first]] / kBN);
+        rte = (int)((a.inst_off[a.inst_pos[p_last] + 1] + kBN - 1) / kBN);
+    }
+    const int rbb = rtb / kBlkTiles;
+    const int nblk_all = (rte + kBlkTiles - 1) / kBlkTiles - rbb;   // blocks of the range
+    const int tile0 = (int)(p_first / kBN);
     const int bps = (nblk_all + a.splits - 1) / a.splits;
     const int b_begin = split * bps;
     const int b_end = b_begin + bps < nblk_all ? b_begin + bps : nblk_all;
     const int nblk = b_end > b_begin ? b_end - b_begin : 0;
-    const int bstart = (tile0 / kBlkTiles + b_begin) % nblk_all;
-    auto blk_at = [&](int u) -> int { return bstart + u >= nblk_all ? bstart + u - nblk_all : bstart + u; };
+    const int bstart = (tile0 / kBlkTiles - rbb + b_begin) % nblk_all;
+    auto blk_at = [&](int u) -> int { return rbb + (bstart + u >= nblk_all ? bstart + u - nblk_all : bstart + u); };
+    // tiles of block cb inside the range
+    auto blk_tiles = [&](int cb) -> int {
+        const int lo = cb * kBlkTiles > rtb ? cb * kBlkTiles : rtb;
+        const int hi = cb * kBlkTiles + kBlkTiles < rte ? cb * kBlkTiles + kBlkTiles : rte;
+        return hi > lo ? hi - lo : 0;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -406,10 +420,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             __syncwarp();
             return true;
         };
-        // tiles in this range (the last block of the operands may be short)
-        int range_tiles = nblk * kBlkTiles;
-        if (nblk > 0 && (nblk_all - 1 - bstart + nblk_all) % nblk_all < nblk)
-            range_tiles -= nblk_all * kBlkTiles - ntile_all;
+        int range_tiles = 0;   // tiles of this split's blocks inside the range
         // A masked sweep whose rows all lie in one component skips the column tiles of
         // that component (every column there is ineligible).
         const uint32_t rcomp = (a.comp && sh->cmin == sh->cmax) ? sh->cmin : kInvalid;
@@ -441,7 +452,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             // thresholds the epilogue learns from it: one tile of pipeline fill per CTA.
             // The wait is bounded; on time-out the decisions only get less selective.
             if (!(COLLECT || a.row_B) && nblk > 0) {
-                first = split == 0 ? tile0 : blk_at(0) * kBlkTiles;
+                first = split == 0 ? tile0 : (blk_at(0) * kBlkTiles > rtb ? blk_at(0) * kBlkTiles : rtb);
                 ok_all = issue(first, 0xFFu);
             }
             if (ok_all && nblk > 0 && lane == 0) {
@@ -457,6 +468,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         for (int u0 = 0; ok_all && u0 < nblk; u0 += 32) {
             const int nb = nblk - u0 < 32 ? nblk - u0 : 32;
             bool bneed = lane < nb;
+            range_tiles += __reduce_add_sync(0xffffffffu, lane < nb ? blk_tiles(blk_at(u0 + lane)) : 0);
             if (lane < nb && a.prune) {
                 const int cb = blk_at(u0 + lane);
                 float lb0, lb1;
@@ -469,8 +481,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 bm &= bm - 1u;
                 const int t0c = blk_at(u0 + q) * kBlkTiles;
                 const int n = ntile_all - t0c < kBlkTiles ? ntile_all - t0c : kBlkTiles;
-                unsigned int wmask = lane < n ? 0xFFu : 0u;
-                if (lane < n) {
+                unsigned int wmask = (lane < n && t0c + lane >= rtb && t0c + lane < rte) ? 0xFFu : 0u;
+                if (wmask) {
                     const int ct = t0c + lane;
                     if (ct == first || (rcomp != kInvalid && a.tile_comp[ct] == rcomp)) {
                         wmask = 0u;
@@ -614,6 +626,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         };
         // The exact walk of one 32-column chunk through this thread's shared-memory row.
         uint32_t tcomp = kInvalid;   // component of the current column tile (kInvalid: mixed)
+        // the columns of this row's instance (all columns when not batched)
+        int64_t ibeg = 0, iend = a.N;
+        if (a.inst_pos && valid) {
+            ibeg = a.inst_off[a.inst_pos[myrow]];
+            iend = a.inst_off[a.inst_pos[myrow] + 1];
+        }
         auto walk = [&](const uint32_t(&w)[32], int64_t jbase) {
             const float thr = COLLECT ? cthr : sel.thr;
             uint32_t mask = 0;
@@ -630,6 +648,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 const int64_t j = jbase + q;
                 if (!(val <= (COLLECT ? cthr : sel.thr))) continue;
                 if (j >= a.N || (uint32_t)j == myrow) continue;
+                if (j < ibeg || j >= iend) continue;   // another instance
                 if (a.comp && (tcomp != kInvalid ? tcomp == mycomp : a.comp_pos[j] == mycomp)) continue;
                 if (COLLECT) {
                     const int64_t sl = slot0 + myrow_slot;

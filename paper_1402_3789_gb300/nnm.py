@@ -61,8 +61,8 @@ class nnm_stats(ctypes.Structure):
 
 
 # every symbol include/nnm.h declares
-EXPORTS = ("nnm_create", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats", "nnm_last_error",
-           "nnm_status_string", "nnm_destroy", "nnm_restrict_static")
+EXPORTS = ("nnm_create", "nnm_create_batched", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats",
+           "nnm_last_error", "nnm_status_string", "nnm_destroy", "nnm_restrict_static")
 STATIC_MAX_ROWS = 1 << 20
 
 _LIB = None
@@ -87,6 +87,9 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.nnm_create.argtypes = [P, i64, i32, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(nnm_options),
                                ctypes.POINTER(P)]
     lib.nnm_create.restype = ctypes.c_int
+    lib.nnm_create_batched.argtypes = [P, P, i64, i32, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(nnm_options),
+                                       ctypes.POINTER(P)]
+    lib.nnm_create_batched.restype = ctypes.c_int
     lib.nnm_nearest.argtypes = [P, i32, P, P]
     lib.nnm_nearest.restype = ctypes.c_int
     lib.nnm_cluster.argtypes = [P, ctypes.POINTER(nnm_restrictions), P, ctypes.POINTER(i64), P,
@@ -125,6 +128,7 @@ class Context:
     d: int
     precision: str
     stream: torch.cuda.Stream
+    offsets: list | None = None   # batched contexts: first row of each instance, and N
 
     def _check(self, status: int):
         if status != NNM_OK:
@@ -148,6 +152,33 @@ def nnm_create(X: torch.Tensor, precision: str = "fp32", stream: torch.cuda.Stre
     if st != NNM_OK:
         raise NNMError(st, "nnm_create failed")
     return Context(h, X, X.shape[0], X.shape[1], precision, stream)
+
+
+def nnm_create_batched(Xs, precision: str = "fp32", stream: torch.cuda.Stream | None = None,
+                       cache_k: int = 0, col_split: int = 0, tile_pruning: bool = True) -> Context:
+    """nnm_create_batched over a list of float32 CUDA tensors [N_b, d_b] (independent
+    instances): they are concatenated into one [sum N_b, max d_b] tensor, narrower ones
+    padded with zero columns (which change no distance).  Row r of instance b is row
+    offsets[b] + r of the context; ``ctx.offsets`` holds the offsets."""
+    lib = load_library()
+    if not Xs or not all(isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.dim() == 2
+                         for x in Xs):
+        raise ValueError("Xs must be float32 [N_b, d_b] CUDA tensors")
+    d = max(x.shape[1] for x in Xs)
+    X = torch.cat([torch.nn.functional.pad(x, (0, d - x.shape[1])) for x in Xs]).contiguous()
+    offsets = [0]
+    for x in Xs:
+        offsets.append(offsets[-1] + x.shape[0])
+    off = (ctypes.c_int64 * len(offsets))(*offsets)
+    stream = stream or torch.cuda.current_stream(X.device)
+    opt = nnm_options(int(cache_k), 0, int(col_split), int(not tile_pruning))
+    h = ctypes.c_void_p()
+    st = lib.nnm_create_batched(ctypes.c_void_p(X.data_ptr()), ctypes.cast(off, ctypes.c_void_p), len(Xs), d, 0,
+                                PRECISIONS[precision], ctypes.c_void_p(stream.cuda_stream), ctypes.byref(opt),
+                                ctypes.byref(h))
+    if st != NNM_OK:
+        raise NNMError(st, "nnm_create_batched failed")
+    return Context(h, X, X.shape[0], d, precision, stream, offsets)
 
 
 def nnm_nearest(ctx: Context, k: int):

@@ -27,7 +27,8 @@ def lib():
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
     assert set(names) == {"nnm_create", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats",
-                          "nnm_last_error", "nnm_status_string", "nnm_destroy", "nnm_restrict_static"}
+                          "nnm_last_error", "nnm_status_string", "nnm_destroy", "nnm_restrict_static",
+                          "nnm_create_batched"}
     for n in names:
         assert hasattr(lib, n), n
     from paper_1402_3789_gb300 import nnm
@@ -70,3 +71,16 @@ def test_struct_layouts_match_the_header(tmp_path):
             ctypes.sizeof(nnm.nnm_options), ctypes.sizeof(nnm.nnm_stats),
             nnm.nnm_stats.max_abs_err.offset, nnm.nnm_stats.scale.offset]
     assert got == want
+
+
+def test_batched_create_rejects_bad_offsets_without_touching_the_gpu(lib):
+    # validation happens before any device work: a dummy X pointer is never read
+    P = ctypes.c_void_p
+    lib.nnm_create_batched.argtypes = [P, P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_int, P, P,
+                                       ctypes.POINTER(P)]
+    lib.nnm_create_batched.restype = ctypes.c_int
+    out = P()
+    for offs in ([1, 5, 9], [0, 5, 5], [0, 7, 3], [0]):
+        arr = (ctypes.c_int64 * len(offs))(*offs)
+        st = lib.nnm_create_batched(P(16), ctypes.cast(arr, P), len(offs) - 1, 4, 0, 0, None, None, ctypes.byref(out))
+        assert st == 1 and not out.value, offs   # NNM_EINVAL

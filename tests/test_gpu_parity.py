@@ -278,3 +278,75 @@ def test_tile_pruning_skips_far_tiles_and_changes_nothing(nnm, orc, precision):
     tree_p, m_p, lab_p, K_p, _ = run_cluster(nnm, X, {"max_join_dist": 3.0}, precision)
     otree, om, olab, oK = orc.cluster(X, {"max_join_dist": 3.0})
     assert np.array_equal(tree_p, otree) and np.array_equal(m_p, om) and np.array_equal(lab_p, olab)
+
+
+# ----------------------------------------------------------------------------------
+# batched contexts: many independent instances in one context
+# ----------------------------------------------------------------------------------
+
+def batched_cases():
+    from paper_1402_3789_gb300.inputs import batched_instances
+    inst = [x for x in batched_instances(count=40, seed=11, n_lo=300, n_hi=3000)][:9]
+    rng = np.random.default_rng(5)
+    inst.insert(3, rng.standard_normal((2, 5)).astype(np.float32))     # two rows
+    inst.insert(6, rng.standard_normal((3, 12)).astype(np.float32))    # three rows
+    inst.append(np.round(rng.standard_normal((700, 6)) * 4).astype(np.float32) / 4)   # ties
+    return inst
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("restr", [{}, {"max_join_dist": 1.2}, {"kl4_min_size": 5, "kl3_max_size": 400},
+                                   {"kl1_stop_clusters": 3, "kl2_max_pre_size": 150}],
+                         ids=["none", "cap", "kl4kl3", "kl1kl2"])
+def test_batched_context_equals_each_instance_alone(nnm, orc, precision, restr):
+    inst = batched_cases()
+    ctx = nnm.nnm_create_batched([dev(x) for x in inst], precision=precision)
+    try:
+        off = ctx.offsets
+        res = nnm.nnm_cluster(ctx, restr)
+        tree = nnm.nnm_get_tree(ctx)
+        merges = res.merges()
+        lab = res.labels.cpu().numpy()
+    finally:
+        nnm.nnm_destroy(ctx)
+    assert tree.shape[0] == off[-1] - len(inst)
+    inst_of = np.searchsorted(np.array(off), np.arange(off[-1]), side="right") - 1
+    total_k = 0
+    for b, X in enumerate(inst):
+        lo = off[b]
+        otree, om, olab, oK = orc.cluster(X, restr)
+        t = tree[inst_of[tree["a"]] == b].copy()
+        t["a"] -= lo
+        t["b"] -= lo
+        assert np.array_equal(t, otree), b
+        m = merges[inst_of[merges["a"]] == b].copy()
+        m["a"] -= lo
+        m["b"] -= lo
+        assert np.array_equal(m, om), b
+        # labels: the same partition, numbered in the same order of smallest members
+        lb = lab[lo:off[b + 1]]
+        _, dense = np.unique(lb, return_inverse=True)
+        first = {}
+        relabel = np.array([first.setdefault(v, len(first)) for v in dense])
+        assert np.array_equal(relabel, olab), b
+        total_k += oK
+    assert res.n_clusters == total_k
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_batched_nearest_stays_inside_instances(nnm, orc, precision):
+    inst = [x for x in batched_cases() if x.shape[0] > 8]
+    ctx = nnm.nnm_create_batched([dev(x) for x in inst], precision=precision)
+    try:
+        off = ctx.offsets
+        idx, D = nnm.nnm_nearest(ctx, 4)
+        idx = idx.cpu().numpy().view(np.uint32)
+        D = D.cpu().numpy()
+        with pytest.raises(nnm.NNMError):
+            nnm.nnm_nearest(ctx, min(x.shape[0] for x in inst))   # k must be < the smallest instance
+    finally:
+        nnm.nnm_destroy(ctx)
+    for b, X in enumerate(inst):
+        oi, oD = orc.knn(X, 4)
+        assert np.array_equal(idx[off[b]:off[b + 1]] - off[b], oi), b
+        assert np.array_equal(D[off[b]:off[b + 1]], oD), b
