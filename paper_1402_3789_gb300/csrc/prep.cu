@@ -274,7 +274,7 @@ __global__ void k_order_from_keys(const nnm_edge *__restrict__ keys, int64_t N, 
     const uint32_t i = keys[p].a;
     pos2row[p] = i;
     row2pos[i] = (uint32_t)p;
-    if (group) group[p] = (uint32_t)(keys[p].D * 0x1p-32);   // the key's high part: its group
+    if (group) group[p] = (uint32_t)(keys[p].D * 0x1p-24);   // the row key's high part: instance, isolated, group
 }
 
 cudaError_t launch_order_from_keys(const nnm_edge *keys, int64_t N, uint32_t *pos2row, uint32_t *row2pos,

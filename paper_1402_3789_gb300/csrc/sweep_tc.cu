@@ -64,25 +64,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait on a phase parity.  Returns false if the wait gave up (time-out, or
-// another role of this CTA already aborted).
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 15) == 0) {
-            if (*abort_flag) return false;
-            if (global_ns() - t0 > kWaitNs) return false;
-        }
-        if (it > 64) __nanosleep(128);
-    }
-}
-
-// Whole-warp bounded wait: every lane polls and the warp decides together, so that no
-// lane waits alone while the others stall at the next warp-wide operation.  Every lane
-// observes the completed phase itself (acquire).
+// Bounded wait on a phase parity by the whole warp: every lane polls and the warp
+// decides together, so that no lane waits alone while the others stall at the next
+// warp-wide operation (a lone waiting lane cost about a thousand cycles per wait).  Every
+// lane observes the completed phase itself (acquire).  Returns false if the wait gave up
+// (time-out, or another role of this CTA already aborted).
 __device__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
 {
     uint64_t t0 = 0;
@@ -398,10 +384,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         // with the epilogue warps that need it
         auto issue = [&](int ct, unsigned int wmask) -> bool {
             const int s = issued % kStages;
-            int ok = 1;
-            if (lane == 0 && issued >= kStages)
-                ok = mbar_wait(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
+            const bool ok = issued < kStages || mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag);
             if (!ok) {
                 *abort_flag = 1;
                 return false;
@@ -530,12 +513,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         int done = 0;
         for (int q = 0;; ++q) {
             const int s = q % kStages, b = q & 1;
-            int ok = 1;
-            if (lane == 0) {
-                ok = mbar_wait(&sh->full[s], (q / kStages) & 1, abort_flag);
-                if (ok && q >= 2) ok = mbar_wait(&sh->tempty[b], ((q >> 1) - 1) & 1, abort_flag);
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
+            bool ok = mbar_wait_warp(&sh->full[s], (q / kStages) & 1, abort_flag);
+            if (ok && q >= 2) ok = mbar_wait_warp(&sh->tempty[b], ((q >> 1) - 1) & 1, abort_flag);
             if (!ok) {
                 *abort_flag = 1;
                 break;
