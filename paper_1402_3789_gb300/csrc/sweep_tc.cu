@@ -24,9 +24,11 @@ namespace nnm {
 namespace {
 
 constexpr int kEpiWarps = 8;
-constexpr int kThreadsTc = (kEpiWarps + 2) * 32;
+constexpr int kThreadsTc = (kEpiWarps + 3) * 32;
 constexpr int kMmaWarp = 8;
 constexpr int kProdWarp = 9;
+constexpr int kPlanWarp = 10;
+constexpr int kPlanQ = 64;        // planned tiles the planner may run ahead of the producer
 constexpr int kBN = 128;          // columns per B tile
 constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere per block)
 constexpr int kMaxStages = 8;
@@ -201,9 +203,12 @@ struct __align__(8) TcShared {
     int nvalid[2];
     unsigned int warps_in[2];    // epilogue warps holding rows of each part (bit masks)
     int npub;                    // epilogue warps that have published a threshold
+    int plan_ct[kPlanQ];         // planned column tiles (-1: end), a ring of kPlanQ ...
+    unsigned int plan_mask[kPlanQ];   // ... with the epilogue warps that need them
+    int plan_head, plan_tail;    // entries written by the planner / taken by the producer
     unsigned int cmin, cmax;     // smallest and largest component among the tile's rows
 };
-constexpr int kShBytes = 640;
+constexpr int kShBytes = 1280;
 static_assert(sizeof(TcShared) <= kShBytes, "shared control block");
 
 // Shared-memory stages of the B ring that fit next to the other regions.
@@ -282,6 +287,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         sh->nvalid[0] = sh->nvalid[1] = 0;
         sh->warps_in[0] = sh->warps_in[1] = 0u;
         sh->npub = 0;
+        sh->plan_head = 0;
+        sh->plan_tail = 0;
         sh->cmin = 0xFFFFFFFFu;
         sh->cmax = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -368,26 +375,35 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     volatile int *abort_flag = &sh->abort_flag;
 
     if (warp == kProdWarp) {
-        // Whole warp walks the column tiles; lane 0 decides, waits and issues.  A tile is
-        // skipped when the lower bound of its candidate values exceeds every row's
-        // threshold (the epilogue's published maxima, possibly stale = larger = safe).
-        // The kept tiles' numbers travel with the stages; -1 ends the sequence.
-        float rhoR[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            rhoR[h] = sh->nvalid[h] > 0 ? sphere_slack(__uint_as_float(sh->rho_bits[h]), __uint_as_float(sh->ymax_bits))
-                                        : -1.0f;
-        const unsigned int win0 = sh->warps_in[0], win1 = sh->warps_in[1];
-        int issued = 0, skipped = 0;
-        bool ok_all = true;
-        // stage the column tile ct (-1: the end marker) into the next slot of the ring,
-        // with the epilogue warps that need it
-        auto issue = [&](int ct, unsigned int wmask) -> bool {
-            const int s = issued % kStages;
-            const bool ok = issued < kStages || mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag);
+        // Producer: takes the planned tiles in order and stages each into the B ring with
+        // the epilogue warps that need it; -1 ends the sequence (and travels with the
+        // stages as the end marker).
+        int issued = 0;
+        for (int taken = 0;; ++taken) {
+            // wait for the planner (bounded; the whole warp polls)
+            const uint64_t t0 = global_ns();
+            bool ok = true;
+            while (((volatile int *)&sh->plan_head)[0] <= taken) {
+                if (*abort_flag || global_ns() - t0 > kWaitNs) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            ok = __all_sync(0xffffffffu, ok);
             if (!ok) {
                 *abort_flag = 1;
-                return false;
+                break;
+            }
+            __threadfence_block();
+            const int ct = ((volatile int *)sh->plan_ct)[taken % kPlanQ];
+            const unsigned int wmask = ((volatile unsigned int *)sh->plan_mask)[taken % kPlanQ];
+            __syncwarp();
+            if (lane == 0) ((volatile int *)&sh->plan_tail)[0] = taken + 1;
+            const int s = issued % kStages;
+            if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag)) {
+                *abort_flag = 1;
+                break;
             }
             if (lane == 0) {
                 sh->ring_tile[s] = ct;
@@ -400,6 +416,55 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 }
             }
             ++issued;
+            __syncwarp();
+            if (ct < 0) break;
+        }
+        // drain: every issued copy must have landed before the CTA exits
+        if (lane == 0) {
+            for (int q = issued - kStages < 0 ? 0 : issued - kStages; q < issued; ++q) {
+                const uint64_t t0 = global_ns();
+                while (!mbar_try_wait(&sh->full[q % kStages], (q / kStages) & 1) && global_ns() - t0 < kWaitNs)
+                    __nanosleep(256);
+            }
+        }
+        __syncwarp();
+    } else if (warp == kPlanWarp) {
+        // Planner: decides which column tiles to take, ahead of the producer (at most
+        // kPlanQ tiles), so that the bound computations overlap the copies and the MMAs.
+        // A tile is skipped when the lower bound of its candidate values exceeds the
+        // threshold of every row that could use it (the epilogue's published maxima,
+        // possibly stale = larger = safe).
+        float rhoR[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            rhoR[h] = sh->nvalid[h] > 0 ? sphere_slack(__uint_as_float(sh->rho_bits[h]), __uint_as_float(sh->ymax_bits))
+                                        : -1.0f;
+        const unsigned int win0 = sh->warps_in[0], win1 = sh->warps_in[1];
+        int planned = 0;
+        bool ok_all = true;
+        // append (ct, wmask) to the plan (bounded wait for room; the whole warp polls)
+        auto push = [&](int ct, unsigned int wmask) -> bool {
+            const uint64_t t0 = global_ns();
+            bool ok = true;
+            while (planned - ((volatile int *)&sh->plan_tail)[0] >= kPlanQ) {
+                if (*abort_flag || global_ns() - t0 > kWaitNs) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) {
+                *abort_flag = 1;
+                return false;
+            }
+            if (lane == 0) {
+                ((volatile int *)sh->plan_ct)[planned % kPlanQ] = ct;
+                ((volatile unsigned int *)sh->plan_mask)[planned % kPlanQ] = wmask;
+                __threadfence_block();
+                ((volatile int *)&sh->plan_head)[0] = planned + 1;
+            }
+            ++planned;
             __syncwarp();
             return true;
         };
@@ -428,7 +493,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                       ? tile_lower_bound(sh->cR[1], rhoR[1], cC, rhoC, a.d, a.lb_R2, a.lb_eps, a.lb_gamma)
                       : INFINITY;
         };
-        int first = -1;   // a tile issued before any decision
+        int first = -1;   // a tile taken before any decision
         if (a.prune) {
             // Without thresholds known at the start, one tile (this row tile's own, the
             // nearest columns) goes unconditionally and every later decision waits for the
@@ -436,7 +501,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             // The wait is bounded; on time-out the decisions only get less selective.
             if (!(COLLECT || a.row_B) && nblk > 0) {
                 first = split == 0 ? tile0 : (blk_at(0) * kBlkTiles > rtb ? blk_at(0) * kBlkTiles : rtb);
-                ok_all = issue(first, 0xFFu);
+                ok_all = push(first, 0xFFu);
             }
             if (ok_all && nblk > 0 && lane == 0) {
                 const uint64_t t0 = global_ns();
@@ -486,25 +551,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                     const int e = __ffs(keepm) - 1;
                     keepm &= keepm - 1u;
                     const unsigned int m = __shfl_sync(0xffffffffu, wmask, e);
-                    if (!(ok_all = issue(t0c + e, m))) break;
+                    if (!(ok_all = push(t0c + e, m))) break;
                 }
             }
         }
-        if (ok_all) issue(-1, 0u);
-        skipped = range_tiles - (issued > 0 ? issued - 1 : 0);
+        if (ok_all) push(-1, 0u);
+        const int taken = planned > 0 ? planned - 1 : 0;   // tiles, without the end marker
         if (lane == 0 && a.st_tiles) {
-            atomicAdd(&a.st_tiles[0], (unsigned long long)skipped);
-            atomicAdd(&a.st_tiles[1], (unsigned long long)(issued > 0 ? issued - 1 : 0));
+            atomicAdd(&a.st_tiles[0], (unsigned long long)(range_tiles - taken));
+            atomicAdd(&a.st_tiles[1], (unsigned long long)taken);
         }
-        // drain: every issued copy must have landed before the CTA exits
-        if (lane == 0) {
-            for (int q = issued - kStages < 0 ? 0 : issued - kStages; q < issued; ++q) {
-                const uint64_t t0 = global_ns();
-                while (!mbar_try_wait(&sh->full[q % kStages], (q / kStages) & 1) && global_ns() - t0 < kWaitNs)
-                    __nanosleep(256);
-            }
-        }
-        __syncwarp();
     } else if (warp == kMmaWarp) {
         const uint32_t idesc = instr_desc(a.fp16);
         const uint32_t lbo = 128, sbo = (uint32_t)(kpad / 8) * 128;
