@@ -28,7 +28,7 @@ constexpr int kThreadsTc = (kEpiWarps + 3) * 32;
 constexpr int kMmaWarp = 8;
 constexpr int kProdWarp = 9;
 constexpr int kPlanWarp = 10;
-constexpr int kPlanQ = 64;        // planned tiles the planner may run ahead of the producer
+constexpr int kPlanQ = 256;       // planned tiles the planner may run ahead of the producer
 constexpr int kBN = 128;          // columns per B tile
 constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere per block)
 constexpr int kMaxStages = 8;
@@ -208,7 +208,7 @@ struct __align__(8) TcShared {
     int plan_head, plan_tail;    // entries written by the planner / taken by the producer
     unsigned int cmin, cmax;     // smallest and largest component among the tile's rows
 };
-constexpr int kShBytes = 1280;
+constexpr int kShBytes = 3072;
 static_assert(sizeof(TcShared) <= kShBytes, "shared control block");
 
 // Shared-memory stages of the B ring that fit next to the other regions.
