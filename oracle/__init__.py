@@ -5,8 +5,9 @@ the CPU-baseline leg of ``bench.py``; the product path never imports it.  It is 
 thin ctypes layer over ``nnm_oracle.c`` (plain C, IEEE binary64, no FMA), which
 shares no code with the CUDA library.
 
-Functions (paper: Litvinenko, arXiv:1402.3789):
-  dist_pairs        Eq. (1) squared, canonical feature order
+Functions (paper: Litvinenko, arXiv:1402.3789); each takes metric= "euclidean" (Eq. (1),
+D its square), "manhattan" or "chebyshev" (the paper leaves other metrics open):
+  dist_pairs        D in the canonical feature order
   knn               exact k nearest neighbours by brute force, order (D, j)
   nnm_batched       the paper's P-minimal-pairs procedure ("General description of
                     the algorithm for constructing the set of minimum distances")
@@ -67,6 +68,8 @@ def _lib():
         lib.or_labels.restype = i64
         lib.or_sort_edges.argtypes = [P, i64]
         lib.or_sort_edges.restype = None
+        lib.or_set_metric.argtypes = [i32]
+        lib.or_set_metric.restype = None
         _LIB = lib
     return _LIB
 
@@ -81,50 +84,69 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def dist_pairs(X, i, j):
+METRICS = {"euclidean": 0, "manhattan": 1, "chebyshev": 2}
+
+
+class _metric:
+    """Select the oracle's metric for one call (back to Euclidean afterwards)."""
+
+    def __init__(self, metric):
+        self.code = METRICS[metric] if isinstance(metric, str) else int(metric)
+
+    def __enter__(self):
+        _lib().or_set_metric(self.code)
+
+    def __exit__(self, *exc):
+        _lib().or_set_metric(0)
+
+
+def dist_pairs(X, i, j, metric="euclidean"):
     """D(i[m], j[m]) for every m: Eq. (1) squared in the canonical order."""
     X, N, d = _rows(X)
     i = np.ascontiguousarray(i, dtype=np.int64)
     j = np.ascontiguousarray(j, dtype=np.int64)
     out = np.empty(i.shape[0], dtype=np.float64)
-    _lib().or_dist_pairs(_ptr(X), d, _ptr(i), _ptr(j), i.shape[0], _ptr(out))
+    with _metric(metric):
+        _lib().or_dist_pairs(_ptr(X), d, _ptr(i), _ptr(j), i.shape[0], _ptr(out))
     return out
 
 
-def knn(X, k, queries=None, threads=0):
+def knn(X, k, queries=None, threads=0, metric="euclidean"):
     """Exact k nearest neighbours (self excluded) of each query row, order (D, j)."""
     X, N, d = _rows(X)
     q = np.arange(N, dtype=np.int64) if queries is None else np.ascontiguousarray(queries, np.int64)
     idx = np.empty((q.shape[0], k), dtype=np.uint32)
     D = np.empty((q.shape[0], k), dtype=np.float64)
-    rc = _lib().or_knn(_ptr(X), N, d, _ptr(q), q.shape[0], k, threads, _ptr(idx), _ptr(D))
+    with _metric(metric):
+        rc = _lib().or_knn(_ptr(X), N, d, _ptr(q), q.shape[0], k, threads, _ptr(idx), _ptr(D))
     if rc != 0:
         raise ValueError("or_knn: bad arguments")
     return idx, D
 
 
-def _edges_call(fn, X, *extra):
+def _edges_call(fn, X, *extra, metric="euclidean"):
     X, N, d = _rows(X)
     out = np.zeros(max(N - 1, 1), dtype=EDGE_DTYPE)
-    m = fn(_ptr(X), N, d, *extra, _ptr(out))
+    with _metric(metric):
+        m = fn(_ptr(X), N, d, *extra, _ptr(out))
     if m < 0:
         raise ValueError(f"{fn.__name__}: bad arguments")
     return out[:m]
 
 
-def nnm_batched(X, P, threads=0):
+def nnm_batched(X, P, threads=0, metric="euclidean"):
     """Merge tree by the paper's batched P-minimal-pairs passes; edges in key order."""
-    return _edges_call(_lib().or_nnm_batched, X, P, threads)
+    return _edges_call(_lib().or_nnm_batched, X, P, threads, metric=metric)
 
 
-def prim(X, threads=0):
+def prim(X, threads=0, metric="euclidean"):
     """Merge tree by dense Prim; edges in key order."""
-    return _edges_call(_lib().or_prim, X, threads)
+    return _edges_call(_lib().or_prim, X, threads, metric=metric)
 
 
-def kruskal_allpairs(X):
+def kruskal_allpairs(X, metric="euclidean"):
     """Merge tree by Kruskal over all pairs (N <= 20000); edges in key order."""
-    return _edges_call(_lib().or_kruskal_allpairs, X)
+    return _edges_call(_lib().or_kruskal_allpairs, X, metric=metric)
 
 
 def _restr(r):
@@ -134,21 +156,23 @@ def _restr(r):
                   int(r.get("kl4_min_size", 0)))
 
 
-def restrict_tree(edges, N, restrictions=None):
+def restrict_tree(edges, N, restrictions=None, metric="euclidean"):
     """Accepted merges (acceptance order) of the key-ordered tree under the restrictions."""
     edges = np.ascontiguousarray(edges, dtype=EDGE_DTYPE)
     out = np.zeros(max(N - 1, 1), dtype=MERGE_DTYPE)
     r = _restr(restrictions)
-    m = _lib().or_restrict_tree(_ptr(edges), edges.shape[0], N, ctypes.byref(r), _ptr(out))
+    with _metric(metric):
+        m = _lib().or_restrict_tree(_ptr(edges), edges.shape[0], N, ctypes.byref(r), _ptr(out))
     return out[:m]
 
 
-def restrict_literal(X, restrictions=None):
+def restrict_literal(X, restrictions=None, metric="euclidean"):
     """Accepted merges when the gates act on every pair in key order (N <= 20000)."""
     X, N, d = _rows(X)
     out = np.zeros(max(N - 1, 1), dtype=MERGE_DTYPE)
     r = _restr(restrictions)
-    m = _lib().or_restrict_literal(_ptr(X), N, d, ctypes.byref(r), _ptr(out))
+    with _metric(metric):
+        m = _lib().or_restrict_literal(_ptr(X), N, d, ctypes.byref(r), _ptr(out))
     if m < 0:
         raise ValueError("or_restrict_literal: bad arguments")
     return out[:m]
@@ -162,15 +186,15 @@ def labels(merges, N):
     return lab, int(K)
 
 
-def cluster(X, restrictions=None, threads=0, method="prim", P=None):
+def cluster(X, restrictions=None, threads=0, method="prim", P=None, metric="euclidean"):
     """Full oracle: merge tree, restrictions, labels -> (tree, merges, labels, K)."""
     X, N, d = _rows(X)
     if method == "prim":
-        tree = prim(X, threads)
+        tree = prim(X, threads, metric=metric)
     elif method == "batched":
-        tree = nnm_batched(X, P if P else N, threads)
+        tree = nnm_batched(X, P if P else N, threads, metric=metric)
     else:
-        tree = kruskal_allpairs(X)
-    merges = restrict_tree(tree, N, restrictions)
+        tree = kruskal_allpairs(X, metric=metric)
+    merges = restrict_tree(tree, N, restrictions, metric=metric)
     lab, K = labels(merges, N)
     return tree, merges, lab, K

@@ -25,19 +25,37 @@
 /* Distance and pair order                                                    */
 /* ------------------------------------------------------------------------- */
 
-/* Eq. (1) ("Overall idea of the algorithm") squared: the features' squared
- * differences summed one after another.  Decisions use the square, which orders
- * pairs the same way as the root. */
+/* The metric of every distance below ("If it is necessary, other metrics could be
+ * chosen", after Eq. (1)); set once before a computation. */
+static int32_t g_metric = OR_EUCLIDEAN;
+
+void or_set_metric(int32_t metric) { g_metric = metric; }
+
+/* D(x, y) with e_k = (double)x_k - (double)y_k in feature order:
+ *   Euclidean: Eq. (1) squared, the e_k^2 summed one after another.  Decisions use
+ *              the square, which orders pairs the same way as the root.
+ *   Manhattan: the |e_k| summed one after another.
+ *   Chebyshev: the largest |e_k|. */
 double or_dist(const float *x, const float *y, int32_t d)
 {
     double s = 0.0;
     for (int32_t k = 0; k < d; ++k) {
         double e = (double)x[k] - (double)y[k];
-        double t = e * e;
-        s = s + t;
+        if (g_metric == OR_MANHATTAN) {
+            s = s + fabs(e);
+        } else if (g_metric == OR_CHEBYSHEV) {
+            double a = fabs(e);
+            if (a > s) s = a;
+        } else {
+            double t = e * e;
+            s = s + t;
+        }
     }
     return s;
 }
+
+/* The length of a pair from its D: the root of a squared Euclidean D, else D. */
+static double pair_length(double D) { return g_metric == OR_EUCLIDEAN ? sqrt(D) : D; }
 
 void or_dist_pairs(const float *X, int32_t d, const int64_t *rows_i, const int64_t *rows_j,
                    int64_t count, double *out)
@@ -551,7 +569,9 @@ static gates_t make_gates(const or_restrictions *r)
 {
     gates_t g;
     g.cap2 = INFINITY;
-    if (r->max_join_dist > 0.0 && isfinite(r->max_join_dist)) g.cap2 = r->max_join_dist * r->max_join_dist;
+    /* the cap in D units: squared for the squared Euclidean D */
+    if (r->max_join_dist > 0.0 && isfinite(r->max_join_dist))
+        g.cap2 = g_metric == OR_EUCLIDEAN ? r->max_join_dist * r->max_join_dist : r->max_join_dist;
     g.kl1 = r->kl1_stop_clusters;
     g.kl2 = r->kl2_max_pre_size;
     g.kl3 = r->kl3_max_size;
@@ -583,7 +603,7 @@ static int walk_step(uf_t *uf, const gates_t *g, const or_edge *e, int phase, in
     mg.a = e->a;
     mg.b = e->b;
     mg.D = e->D;
-    mg.dist = sqrt(e->D);
+    mg.dist = pair_length(e->D);
     mg.new_size = uf->size[r];
     out[(*m)++] = mg;
     --*K;

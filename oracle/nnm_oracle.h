@@ -54,7 +54,15 @@ typedef struct {
     int64_t kl4_min_size;
 } or_restrictions;
 
-/* Eq. (1) squared, canonical order. */
+/* Metrics: Eq. (1) (its square is D), and the two the paper leaves open to choose. */
+#define OR_EUCLIDEAN 0
+#define OR_MANHATTAN 1
+#define OR_CHEBYSHEV 2
+
+/* The metric of all later calls (default OR_EUCLIDEAN). */
+void or_set_metric(int32_t metric);
+
+/* D(x, y) in the canonical order (Eq. (1) squared for OR_EUCLIDEAN). */
 double or_dist(const float *x, const float *y, int32_t d);
 
 /* Fill out[m] = D(rows_i[m], rows_j[m]) for m < count. */

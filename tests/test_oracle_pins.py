@@ -429,3 +429,80 @@ def test_labels_partition_and_order(oracle_mod):
     assert np.array_equal(lab, seen)   # BFS from increasing seeds numbers clusters by smallest member
     first = [int(np.nonzero(lab == c)[0][0]) for c in range(K)]
     assert first == sorted(first)
+
+
+# ----------------------------------------------------------------------------------
+# other metrics (the paper: "If it is necessary, other metrics could be chosen")
+# ----------------------------------------------------------------------------------
+
+def metric_by_hand(x, y, metric):
+    """Python floats (binary64), feature order: the definitions written out."""
+    s = 0.0
+    for a, b in zip(x.tolist(), y.tolist()):
+        e = float(a) - float(b)
+        if metric == "manhattan":
+            s = s + abs(e)
+        else:
+            s = max(s, abs(e))
+    return s
+
+
+def test_metric_values_by_hand(oracle_mod):
+    # (0,0), (3,4), (1,-2): |3|+|4| = 7, |1|+|2| = 3, |2|+|6| = 8; max: 4, 2, 6
+    X = np.array([[0, 0], [3, 4], [1, -2]], np.float32)
+    i, j = [0, 0, 1], [1, 2, 2]
+    assert oracle_mod.dist_pairs(X, i, j, metric="manhattan").tolist() == [7.0, 3.0, 8.0]
+    assert oracle_mod.dist_pairs(X, i, j, metric="chebyshev").tolist() == [4.0, 2.0, 6.0]
+    assert oracle_mod.dist_pairs(X, i, j).tolist() == [25.0, 5.0, 40.0]   # Euclidean unchanged
+
+
+@pytest.mark.parametrize("metric", ["manhattan", "chebyshev"])
+def test_metric_matches_definition_and_norm_order(oracle_mod, metric):
+    rng = np.random.default_rng(21)
+    X = (rng.standard_normal((60, 13)) * rng.uniform(0.1, 50, 13)).astype(np.float32)
+    i, j = np.triu_indices(60, 1)
+    D = oracle_mod.dist_pairs(X, i, j, metric=metric)
+    want = [metric_by_hand(X[a], X[b], metric) for a, b in zip(i, j)]
+    assert D.tolist() == want
+    # |v|_inf <= |v|_2 <= |v|_1 <= sqrt(d) |v|_2 (a dropped term or sign would break one)
+    L2 = np.sqrt(oracle_mod.dist_pairs(X, i, j))
+    tol = 1e-12 * L2
+    if metric == "manhattan":
+        assert np.all(D >= L2 - tol) and np.all(D <= np.sqrt(13) * L2 + tol)
+    else:
+        assert np.all(D <= L2 + tol) and np.all(D >= L2 / np.sqrt(13) - tol)
+
+
+@pytest.mark.parametrize("metric", ["manhattan", "chebyshev"])
+def test_metric_knn_and_trees(oracle_mod, metric):
+    rng = np.random.default_rng(22)
+    X = grid_points(rng, 200, 4, lim=20)   # many equal distances: the tie-break decides
+    idx, D = oracle_mod.knn(X, 5, metric=metric)
+    for r in range(0, 200, 17):
+        cand = sorted((metric_by_hand(X[r], X[c], metric), c) for c in range(200) if c != r)[:5]
+        assert [c for _, c in cand] == idx[r].tolist()
+        assert [v for v, _ in cand] == D[r].tolist()
+    ref = oracle_mod.kruskal_allpairs(X, metric=metric)
+    tree_checks(X, ref)
+    for e in (oracle_mod.prim(X, metric=metric), oracle_mod.nnm_batched(X, 7, metric=metric)):
+        assert np.array_equal(e, ref)
+    # the lightest pair at every row is a tree edge (cut property under any metric)
+    keys = set(zip(ref["a"].tolist(), ref["b"].tolist()))
+    for r in range(200):
+        c = int(idx[r, 0])
+        assert (min(r, c), max(r, c)) in keys
+
+
+def test_metric_cap_and_reported_length(oracle_mod):
+    # three points on a line, 1.0 apart: D = 1 under every metric (squared: 1 as well),
+    # but the cap compares D with c itself for L1/Linf and with c^2 for Euclidean
+    X = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [1.0, 3.0]], np.float32)
+    for metric in ("manhattan", "chebyshev"):
+        tree = oracle_mod.kruskal_allpairs(X, metric=metric)
+        m = oracle_mod.restrict_tree(tree, 4, {"max_join_dist": 1.0}, metric=metric)
+        assert len(m) == 2 and np.all(m["dist"] == m["D"])   # length = D itself
+        m2 = oracle_mod.restrict_tree(tree, 4, {"max_join_dist": 2.0}, metric=metric)
+        assert len(m2) == 3   # the last pair is 2.0 away: D <= 2.0 admits it
+    tree = oracle_mod.kruskal_allpairs(X)
+    m = oracle_mod.restrict_tree(tree, 4, {"max_join_dist": 2.0})
+    assert len(m) == 3 and m["D"][-1] == 4.0 and m["dist"][-1] == 2.0   # D <= 2.0^2
