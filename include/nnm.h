@@ -46,8 +46,14 @@ typedef enum {
     NNM_EUNSUPPORTED = 6  /* metric / precision / size not provided by this build          */
 } nnm_status;
 
-/* Eq. (1) is the default; "If it is necessary, other metrics could be chosen". */
-typedef enum { NNM_EUCLIDEAN = 0 } nnm_metric;
+/* Eq. (1) is the default; "If it is necessary, other metrics could be chosen".  With
+ * e_k = (double)x_ik - (double)x_jk in feature order, binary64, no contraction:
+ *   NNM_EUCLIDEAN  D = sum of e_k^2 (Eq. (1) squared); a merge's length is sqrt(D) and the
+ *                  maximum joining distance c admits D <= c*c.
+ *   NNM_MANHATTAN  D = sum of |e_k|;  NNM_CHEBYSHEV  D = max |e_k|.  For these two the
+ *                  length is D itself and c admits D <= c.  They use the FP32 direct
+ *                  candidates (NNM_PREC_FP32); other precisions give EUNSUPPORTED. */
+typedef enum { NNM_EUCLIDEAN = 0, NNM_MANHATTAN = 1, NNM_CHEBYSHEV = 2 } nnm_metric;
 
 /* How candidate distances are produced before the exact binary64 re-rank.  Every
  * precision returns the same, exact result; they differ only in speed.
@@ -155,7 +161,7 @@ typedef struct {
  *   X_dev   row-major float32 [N][d] on the device; borrowed: it must stay alive and
  *           unchanged until nnm_destroy (the exact re-rank reads it).
  *   N       rows, 1 <= N < 2^31.   d  features, 1 <= d <= 32.
- *   metric  NNM_EUCLIDEAN.          precision  see nnm_precision.
+ *   metric  see nnm_metric.         precision  see nnm_precision.
  *   cuda_stream  cudaStream_t to enqueue on (NULL: the legacy default stream).
  *   options      may be NULL.
  *   out     receives the context (NULL on failure).

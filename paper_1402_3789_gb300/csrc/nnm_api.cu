@@ -83,6 +83,7 @@ struct nnm_ctx {
     float *heavy_thr = nullptr, *heavy_thr2 = nullptr;
     size_t heavy_cap = 0;        // rows
     // cache and rounds
+    int metric = 0;   // nnm_metric
     int kc = 0;   // cache width (neighbours kept per row by the first sweep)
     int kr = 0;   // neighbours kept by a rescan (<= kc)
     uint32_t *cache_j = nullptr;
@@ -299,6 +300,7 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.tile_c = c->tile_c;
     a.tile_rho = c->tile_rho;
     a.group = c->group;
+    a.metric = c->metric;
     a.inst_pos = c->inst_pos;
     a.inst_off = c->inst_off;
     a.blk_c = c->blk_c;
@@ -811,6 +813,7 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     st.X = c->X;
     st.d = c->d;
     st.inst_pos = c->inst_pos;
+    st.metric = c->metric;
     st.row_D = c->row_D;
     st.row_ab = c->row_ab;
     st.row_state = c->row_state;
@@ -955,7 +958,9 @@ static nnm_status create_impl(const float *X_dev, int64_t N, int32_t d, const in
     if (!out) return NNM_EINVAL;
     *out = nullptr;
     if (!X_dev || N < 1 || N >= (int64_t(1) << 31) || d < 1 || d > 32) return NNM_EINVAL;
-    if (metric != NNM_EUCLIDEAN) return NNM_EUNSUPPORTED;
+    if (metric != NNM_EUCLIDEAN && metric != NNM_MANHATTAN && metric != NNM_CHEBYSHEV) return NNM_EUNSUPPORTED;
+    // the tensor-core candidates rest on |x|^2 + |y|^2 - 2 x.y: Euclidean only
+    if (metric != NNM_EUCLIDEAN && precision != NNM_PREC_FP32) return NNM_EUNSUPPORTED;
     if (precision != NNM_PREC_FP32 && precision != NNM_PREC_BF16_RERANK && precision != NNM_PREC_FP16_RERANK &&
         precision != NNM_PREC_BF16X3_RERANK)
         return NNM_EUNSUPPORTED;
@@ -974,6 +979,8 @@ static nnm_status create_impl(const float *X_dev, int64_t N, int32_t d, const in
     c->N = N;
     c->d = d;
     c->prec = precision;
+    c->metric = (int)metric;
+    c->margin.metric = (int)metric;
     if (options) c->opt = *options;
     c->stream = (cudaStream_t)cuda_stream;
     c->kc = c->opt.cache_k > 0 ? c->opt.cache_k : (precision == NNM_PREC_BF16_RERANK ? 2 : 8);
@@ -1058,8 +1065,10 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
         return fail(c, NNM_EINVAL, "negative restriction");
     if (r.kl2_max_pre_size > 0 && r.kl3_max_size > 0 && r.kl3_max_size <= r.kl2_max_pre_size)
         return fail(c, NNM_EINVAL, "KL3 must exceed KL2");
-    const double cap2 = (r.max_join_dist > 0.0 && isfinite(r.max_join_dist)) ? r.max_join_dist * r.max_join_dist
-                                                                             : INFINITY;
+    // the cap in D units: squared for the squared Euclidean D, else the length itself
+    const double cap2 = (r.max_join_dist > 0.0 && isfinite(r.max_join_dist))
+                            ? (c->metric == NNM_EUCLIDEAN ? r.max_join_dist * r.max_join_dist : r.max_join_dist)
+                            : INFINITY;
     reset_stats(c);
     {
         Phase total(c, &c->stats.ms_total);
@@ -1082,6 +1091,7 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
             ra.n_merges = &c->dstat[4];
             ra.err_flag = &c->derr[3];
             ra.n_inst = c->n_inst;
+            ra.metric = c->metric;
             ra.inst_off = c->inst_off;
             ra.ebeg = c->ebeg;
             ra.eend = c->eend;

@@ -27,21 +27,26 @@ constexpr uint8_t kCacheFull = 0;      // k found: every other eligible column h
 constexpr uint8_t kCacheAll = 1;       // fewer found: they are every eligible column
 constexpr uint8_t kCacheBounded = 2;   // fewer found: every other eligible column has D > the row's bound
 
-// The exact squared distance of Eq. (1): D = ((t_0 + t_1) + ...) + t_{d-1},
-// t_k = e_k * e_k, e_k = x_ik - x_jk, each operation binary64 round-to-nearest, no
-// contraction (the same value for (i, j) and (j, i)).
-__device__ __forceinline__ double canon_D(const float *__restrict__ xi, const float *__restrict__ xj, int d)
+// The exact D of a pair, e_k = x_ik - x_jk, each operation binary64 round-to-nearest,
+// no contraction (the same value for (i, j) and (j, i)):
+//   Euclidean (metric 0): Eq. (1) squared, ((t_0 + t_1) + ...) + t_{d-1}, t_k = e_k * e_k;
+//   Manhattan (1): ((|e_0| + |e_1|) + ...) + |e_{d-1}|;  Chebyshev (2): max |e_k|.
+__device__ __forceinline__ double canon_D(const float *__restrict__ xi, const float *__restrict__ xj, int d,
+                                          int metric = 0)
 {
     double s = 0.0;
     for (int k = 0; k < d; ++k) {
         const double e = __dsub_rn((double)xi[k], (double)xj[k]);
-        s = __dadd_rn(s, __dmul_rn(e, e));
+        if (metric == 1) s = __dadd_rn(s, fabs(e));
+        else if (metric == 2) s = fmax(s, fabs(e));
+        else s = __dadd_rn(s, __dmul_rn(e, e));
     }
     return s;
 }
 
 struct Margin {
     int tensor;         // 0: FP32 direct candidates; 1: tensor-core candidates
+    int metric;         // 0 Euclidean (D squared), 1 Manhattan, 2 Chebyshev
     double gamma;       // relative error bound of one candidate value
     double alpha;       // absolute slack (underflow)
     double R;           // tensor: max rounding radius over rows (scaled units)
@@ -87,6 +92,7 @@ struct SweepArgs {
     const uint32_t *comp_pos;   // with comp: component of each position
     const uint32_t *tile_comp;  // with comp: component of each column tile of tile_w
                                 // positions when they all share one, else kInvalid
+    int metric;               // FP32 path: 0 Euclidean (squared), 1 Manhattan, 2 Chebyshev
     const double *row_B;      // per original row: only columns with exact D <= row_B are
                               // wanted (nullptr: no bound); a bound lowers the starting
                               // threshold of the row
@@ -142,8 +148,11 @@ __device__ __forceinline__ float sphere_slack(float rho, float ymax)
 // of the sphere (cC, rhoC)): |y_i - y_j| >= |cR - cC| - rhoR - rhoC, the 16-bit operands
 // differ from y by at most R each, and a candidate value differs from the squared
 // operand distance by at most lb_eps (tensor) or a relative lb_gamma (FP32).
+// Other metrics (FP32 path only): the Euclidean gap bounds them too, since
+// |v|_1 >= |v|_2 and |v|_inf >= |v|_2 / sqrt(d); the candidate value is then the gap
+// (Manhattan) or gap / sqrt(d) (Chebyshev) instead of its square.
 __device__ __forceinline__ float tile_lower_bound(const float *cR, float rhoR, const float *cC, float rhoC, int d,
-                                                  float lb_R2, float lb_eps, float lb_gamma)
+                                                  float lb_R2, float lb_eps, float lb_gamma, int metric = 0)
 {
     // fully unrolled so that the (predicated) loads of cC issue together
     float c[32];
@@ -160,7 +169,8 @@ __device__ __forceinline__ float tile_lower_bound(const float *cR, float rhoR, c
     const float dist = sqrtf(s) * (1.0f - 0x1p-12f);
     const float gap = dist - rhoR - rhoC - lb_R2;
     if (!(gap > 0.0f)) return -INFINITY;
-    const float sq = gap * gap * (1.0f - 0x1p-12f);
+    const float sq = metric == 0 ? gap * gap * (1.0f - 0x1p-12f)
+                     : (metric == 1 ? gap : gap * rsqrtf((float)d) * (1.0f - 0x1p-12f));
     return sq * (1.0f - lb_gamma) - lb_eps;
 }
 
@@ -307,6 +317,7 @@ struct RoundState {
     double overscan;               // rescan bound = overscan * the component's bound
     const float *X;                // [N][d] the rows (exact distances of the bound search)
     int d;
+    int metric;
     const uint32_t *inst_pos;      // batched contexts: instance of each position (nullable)
     unsigned long long *row_D;     // [N] key of the row's best outgoing candidate (D bits)
     unsigned long long *row_ab;    // [N] (min << 32) | max
@@ -355,6 +366,7 @@ struct RestrictArgs {
     nnm_merge *merges;         // [N-1] out
     unsigned long long *n_merges; // device out
     int *err_flag;
+    int metric;                // a merge's length: sqrt(D) (Euclidean) or D
     // batched contexts: one walk per instance (CTA b), the edges sorted by (instance,
     // key); instance b = rows [inst_off[b], inst_off[b+1]), edges [ebeg[b], eend[b]).
     // Each walk writes its merges at merges_tmp[ebeg[b]..] and their count to inst_nm[b];

@@ -128,13 +128,21 @@ __device__ void select_topk(double *wD, uint32_t *wj, int n, int k, int stride, 
     *n_out = cnt;
 }
 
-// FP32 direct squared distance, one FMA per feature in order (|s - exact| <= gamma32*s + alpha32).
-__device__ __forceinline__ float fp32_D(const float *__restrict__ xi, const float *__restrict__ xj, int d)
+// FP32 direct value of D, features in order, as the FP32 sweep computes it: one FMA per
+// feature for the squared Euclidean distance, a sum of |e| for Manhattan, a running
+// max of |e| for Chebyshev (|s - exact| <= gamma32*s + alpha32 in every case).
+__device__ __forceinline__ float fp32_D(const float *__restrict__ xi, const float *__restrict__ xj, int d, int metric)
 {
     float s = 0.0f;
-    for (int k = 0; k < d; ++k) {
-        const float e = xi[k] - xj[k];
-        s = fmaf(e, e, s);
+    if (metric == 1) {
+        for (int k = 0; k < d; ++k) s += fabsf(xi[k] - xj[k]);
+    } else if (metric == 2) {
+        for (int k = 0; k < d; ++k) s = fmaxf(s, fabsf(xi[k] - xj[k]));
+    } else {
+        for (int k = 0; k < d; ++k) {
+            const float e = xi[k] - xj[k];
+            s = fmaf(e, e, s);
+        }
     }
     return s;
 }
@@ -153,7 +161,7 @@ __device__ int exact_distances(const float *xi, const float *X, int d, double *w
     if (refine) {
         // float keys of s in place of the marks (+inf keys for non-candidates)
         for (int e = lane; e < n; e += 32)
-            kk[e] = kk[e] < kInfD ? (long long)__float_as_int(fp32_D(xi, X + (int64_t)wj[e] * d, d)) : kNone;
+            kk[e] = kk[e] < kInfD ? (long long)__float_as_int(fp32_D(xi, X + (int64_t)wj[e] * d, d, m.metric)) : kNone;
         __syncwarp();
         int taken = 0;
         const float vk = kth_float(kk, n, k, &taken);
@@ -171,7 +179,7 @@ __device__ int exact_distances(const float *xi, const float *X, int d, double *w
     for (int e = lane; e < n; e += 32) {
         double D = INFINITY;
         if (kk[e] == 0LL) {
-            D = canon_D(xi, X + (int64_t)wj[e] * d, d);
+            D = canon_D(xi, X + (int64_t)wj[e] * d, d, m.metric);
             ++nd;
         }
         wD[e] = D;

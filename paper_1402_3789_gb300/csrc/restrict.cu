@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
                     mg.a = ed.a;
                     mg.b = ed.b;
                     mg.D = ed.D;
-                    mg.dist = sqrt(ed.D);
+                    mg.dist = a.metric == 0 ? sqrt(ed.D) : ed.D;
                     mg.new_size = S.newsize[e];
                     merges[n_out + S.scan1[e]] = mg;
                 } else if (S.dec[e] == 2) {

@@ -155,7 +155,7 @@ __global__ void k_flag(RoundState st)
                     if (st.inst_pos && st.inst_pos[q] != st.inst_pos[p]) break;   // another instance
                     const uint32_t j = st.pos2row[q];
                     if (st.comp[j] == c) continue;
-                    const double D = canon_D(xi, st.X + (int64_t)j * st.d, st.d);
+                    const double D = canon_D(xi, st.X + (int64_t)j * st.d, st.d, st.metric);
                     atomicMin(&st.comp_bound[c], (unsigned long long)__double_as_longlong(D));
                     break;
                 }

@@ -17,6 +17,8 @@
 // underflow term, s the exact squared distance of the FP32 inputs.
 #include <cuda_pipeline_primitives.h>
 
+#include <type_traits>
+
 #include "select.cuh"
 
 namespace nnm {
@@ -187,7 +189,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
                                     const float rc = a.tile_rho[ct * 2 + hc];
                                     if (rc >= 0.0f)
                                         lb[h] = fminf(lb[h], tile_lower_bound(cR[h], rhoR[h], a.tile_c + (ct * 2 + hc) * a.d,
-                                                                              rc, a.d, 0.0f, a.lb_eps, a.lb_gamma));
+                                                                              rc, a.d, 0.0f, a.lb_eps, a.lb_gamma,
+                                                                              a.metric));
                                 }
                         }
                     }
@@ -288,41 +291,57 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
         // rows of the tile's own component have nothing eligible in it
         const bool own0 = !valid[0] || (a.comp && tcomp != kInvalid && tcomp == crow[0]);
         const bool own1 = !valid[1] || (a.comp && tcomp != kInvalid && tcomp == crow[1]);
-        for (int c = (own0 && own1) ? n : 0; c < n; c += 2) {
-            const float4 *ya = reinterpret_cast<const float4 *>(ys + c * DP);
-            const float4 *yb = reinterpret_cast<const float4 *>(ys + (c + 1) * DP);
-            float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+        // the column loop, one copy per metric (the branch is outside the loop)
+        auto columns = [&](auto metric_tag) {
+            constexpr int M = decltype(metric_tag)::value;
+            for (int c = (own0 && own1) ? n : 0; c < n; c += 2) {
+                const float4 *ya = reinterpret_cast<const float4 *>(ys + c * DP);
+                const float4 *yb = reinterpret_cast<const float4 *>(ys + (c + 1) * DP);
+                float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
 #pragma unroll
-            for (int q = 0; q < DP / 4; ++q) {
-                const float4 A = ya[q], B = yb[q];
-                const float av[4] = {A.x, A.y, A.z, A.w};
-                const float bv[4] = {B.x, B.y, B.z, B.w};
+                for (int q = 0; q < DP / 4; ++q) {
+                    const float4 A = ya[q], B = yb[q];
+                    const float av[4] = {A.x, A.y, A.z, A.w};
+                    const float bv[4] = {B.x, B.y, B.z, B.w};
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const int k = q * 4 + w;
-                    if (k < D) {
-                        float e;
-                        e = x[0][k] - av[w];
-                        s00 = fmaf(e, e, s00);
-                        e = x[0][k] - bv[w];
-                        s01 = fmaf(e, e, s01);
-                        e = x[1][k] - av[w];
-                        s10 = fmaf(e, e, s10);
-                        e = x[1][k] - bv[w];
-                        s11 = fmaf(e, e, s11);
+                    for (int w = 0; w < 4; ++w) {
+                        const int k = q * 4 + w;
+                        if (k < D) {
+                            const float e00 = x[0][k] - av[w], e01 = x[0][k] - bv[w];
+                            const float e10 = x[1][k] - av[w], e11 = x[1][k] - bv[w];
+                            if constexpr (M == 0) {   // Euclidean: e^2 summed (one FMA)
+                                s00 = fmaf(e00, e00, s00);
+                                s01 = fmaf(e01, e01, s01);
+                                s10 = fmaf(e10, e10, s10);
+                                s11 = fmaf(e11, e11, s11);
+                            } else if constexpr (M == 1) {   // Manhattan: |e| summed
+                                s00 += fabsf(e00);
+                                s01 += fabsf(e01);
+                                s10 += fabsf(e10);
+                                s11 += fabsf(e11);
+                            } else {   // Chebyshev: largest |e|
+                                s00 = fmaxf(s00, fabsf(e00));
+                                s01 = fmaxf(s01, fabsf(e01));
+                                s10 = fmaxf(s10, fabsf(e10));
+                                s11 = fmaxf(s11, fabsf(e11));
+                            }
+                        }
                     }
                 }
+                if ((s00 <= th0) | (s01 <= th0) | (s10 <= th1) | (s11 <= th1)) {
+                    const uint32_t ja = (uint32_t)(j0 + c), jb = ja + 1;
+                    consider(0, s00, ja);
+                    consider(0, s01, jb);
+                    consider(1, s10, ja);
+                    consider(1, s11, jb);
+                    th0 = COLLECT ? cthr[0] : sel[0].thr;
+                    th1 = COLLECT ? cthr[1] : sel[1].thr;
+                }
             }
-            if ((s00 <= th0) | (s01 <= th0) | (s10 <= th1) | (s11 <= th1)) {
-                const uint32_t ja = (uint32_t)(j0 + c), jb = ja + 1;
-                consider(0, s00, ja);
-                consider(0, s01, jb);
-                consider(1, s10, ja);
-                consider(1, s11, jb);
-                th0 = COLLECT ? cthr[0] : sel[0].thr;
-                th1 = COLLECT ? cthr[1] : sel[1].thr;
-            }
-        }
+        };
+        if (a.metric == 1) columns(std::integral_constant<int, 1>{});
+        else if (a.metric == 2) columns(std::integral_constant<int, 2>{});
+        else columns(std::integral_constant<int, 0>{});
         if (!COLLECT && a.splits > 1) {
 #pragma unroll
             for (int r = 0; r < 2; ++r)

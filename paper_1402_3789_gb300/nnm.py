@@ -136,9 +136,12 @@ class Context:
             raise NNMError(status, (msg or b"").decode())
 
 
+METRICS = {"euclidean": 0, "manhattan": 1, "chebyshev": 2}
+
+
 def nnm_create(X: torch.Tensor, precision: str = "fp32", stream: torch.cuda.Stream | None = None,
                cache_k: int = 0, freeze_at_cap: bool = False, col_split: int = 0,
-               tile_pruning: bool = True) -> Context:
+               tile_pruning: bool = True, metric: str = "euclidean") -> Context:
     """nnm_create: X is a contiguous float32 [N, d] CUDA tensor (kept alive by the context)."""
     lib = load_library()
     if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
@@ -147,7 +150,7 @@ def nnm_create(X: torch.Tensor, precision: str = "fp32", stream: torch.cuda.Stre
     stream = stream or torch.cuda.current_stream(X.device)
     opt = nnm_options(int(cache_k), int(bool(freeze_at_cap)), int(col_split), int(not tile_pruning))
     h = ctypes.c_void_p()
-    st = lib.nnm_create(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], 0, PRECISIONS[precision],
+    st = lib.nnm_create(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], METRICS[metric], PRECISIONS[precision],
                         ctypes.c_void_p(stream.cuda_stream), ctypes.byref(opt), ctypes.byref(h))
     if st != NNM_OK:
         raise NNMError(st, "nnm_create failed")
@@ -155,7 +158,8 @@ def nnm_create(X: torch.Tensor, precision: str = "fp32", stream: torch.cuda.Stre
 
 
 def nnm_create_batched(Xs, precision: str = "fp32", stream: torch.cuda.Stream | None = None,
-                       cache_k: int = 0, col_split: int = 0, tile_pruning: bool = True) -> Context:
+                       cache_k: int = 0, col_split: int = 0, tile_pruning: bool = True,
+                       metric: str = "euclidean") -> Context:
     """nnm_create_batched over a list of float32 CUDA tensors [N_b, d_b] (independent
     instances): they are concatenated into one [sum N_b, max d_b] tensor, narrower ones
     padded with zero columns (which change no distance).  Row r of instance b is row
@@ -173,7 +177,8 @@ def nnm_create_batched(Xs, precision: str = "fp32", stream: torch.cuda.Stream | 
     stream = stream or torch.cuda.current_stream(X.device)
     opt = nnm_options(int(cache_k), 0, int(col_split), int(not tile_pruning))
     h = ctypes.c_void_p()
-    st = lib.nnm_create_batched(ctypes.c_void_p(X.data_ptr()), ctypes.cast(off, ctypes.c_void_p), len(Xs), d, 0,
+    st = lib.nnm_create_batched(ctypes.c_void_p(X.data_ptr()), ctypes.cast(off, ctypes.c_void_p), len(Xs), d,
+                                METRICS[metric],
                                 PRECISIONS[precision], ctypes.c_void_p(stream.cuda_stream), ctypes.byref(opt),
                                 ctypes.byref(h))
     if st != NNM_OK:

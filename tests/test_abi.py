@@ -52,7 +52,9 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert lib.nnm_create(dummy, 10, 0, 0, 0, None, None, ctypes.byref(out)) == 1     # d < 1
     assert lib.nnm_create(None, 10, 4, 0, 0, None, None, ctypes.byref(out)) == 1      # null X
     assert lib.nnm_create(dummy, 1 << 31, 4, 0, 0, None, None, ctypes.byref(out)) == 1
-    assert lib.nnm_create(dummy, 10, 4, 1, 0, None, None, ctypes.byref(out)) == 6     # metric
+    assert lib.nnm_create(dummy, 10, 4, 3, 0, None, None, ctypes.byref(out)) == 6     # metric
+    assert lib.nnm_create(dummy, 10, 4, 1, 1, None, None, ctypes.byref(out)) == 6     # Manhattan on tensor cores
+    assert lib.nnm_create(dummy, 10, 4, 2, 3, None, None, ctypes.byref(out)) == 6     # Chebyshev on tensor cores
     assert lib.nnm_create(dummy, 10, 4, 0, 7, None, None, ctypes.byref(out)) == 6     # precision
     assert lib.nnm_create(dummy, 10, 31, 0, 3, None, None, ctypes.byref(out)) == 6    # split form: d <= 30
 

@@ -350,3 +350,75 @@ def test_batched_nearest_stays_inside_instances(nnm, orc, precision):
         oi, oD = orc.knn(X, 4)
         assert np.array_equal(idx[off[b]:off[b + 1]] - off[b], oi), b
         assert np.array_equal(D[off[b]:off[b + 1]], oD), b
+
+
+# ----------------------------------------------------------------------------------
+# other metrics: Manhattan and Chebyshev on the FP32 direct path
+# ----------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("metric", ["manhattan", "chebyshev"])
+@pytest.mark.parametrize("case", ["mixture", "grid_ties", "wide_offsets"])
+def test_other_metrics_nearest_and_tree(nnm, orc, metric, case):
+    rng = np.random.default_rng(31)
+    if case == "mixture":
+        X = make("nnm_n4096_d8", 3001, seed=7)
+    elif case == "grid_ties":
+        X = (rng.integers(0, 6, (2500, 5)) / 4.0).astype(np.float32)   # many equal distances
+    else:
+        X = (rng.standard_normal((1800, 11)) * rng.uniform(0.01, 300, 11) + 1000).astype(np.float32)
+    ctx = nnm.nnm_create(dev(X), precision="fp32", metric=metric)
+    try:
+        idx, D = nnm.nnm_nearest(ctx, 6)
+        idx = idx.cpu().numpy().view(np.uint32)
+        D = D.cpu().numpy()
+        restr = {"max_join_dist": 2.5, "kl4_min_size": 4}
+        res = nnm.nnm_cluster(ctx, restr)
+        tree = nnm.nnm_get_tree(ctx)
+        merges = res.merges()
+        lab = res.labels.cpu().numpy()
+    finally:
+        nnm.nnm_destroy(ctx)
+    oi, oD = orc.knn(X, 6, metric=metric)
+    assert np.array_equal(idx, oi) and np.array_equal(D, oD)
+    otree, om, olab, oK = orc.cluster(X, restr, metric=metric)
+    assert np.array_equal(tree, otree)
+    assert np.array_equal(merges, om)
+    assert np.array_equal(lab, olab) and res.n_clusters == oK
+
+
+@pytest.mark.parametrize("metric", ["manhattan", "chebyshev"])
+def test_other_metrics_batched_and_pruning(nnm, orc, metric):
+    rng = np.random.default_rng(32)
+    inst = [make("nnm_n4096_d8", 900, seed=s) for s in range(3)] + [rng.standard_normal((5, 8)).astype(np.float32)]
+    ctx = nnm.nnm_create_batched([dev(x) for x in inst], precision="fp32", metric=metric)
+    try:
+        off = ctx.offsets
+        nnm.nnm_cluster(ctx, {})
+        tree = nnm.nnm_get_tree(ctx)
+    finally:
+        nnm.nnm_destroy(ctx)
+    inst_of = np.searchsorted(np.array(off), np.arange(off[-1]), side="right") - 1
+    for b, X in enumerate(inst):
+        t = tree[inst_of[tree["a"]] == b].copy()
+        t["a"] -= off[b]
+        t["b"] -= off[b]
+        assert np.array_equal(t, orc.prim(X, metric=metric)), b
+    # well separated blobs: the Euclidean sphere bound prunes for these metrics too
+    centres = rng.uniform(0, 400, (16, 6))
+    X = (centres[rng.integers(0, 16, 6000)] + rng.standard_normal((6000, 6))).astype(np.float32)
+    ctx = nnm.nnm_create(dev(X), precision="fp32", metric=metric, col_split=1)
+    try:
+        idx, D = nnm.nnm_nearest(ctx, 3)
+        st = nnm.nnm_get_stats(ctx)
+    finally:
+        nnm.nnm_destroy(ctx)
+    oi, oD = orc.knn(X, 3, metric=metric)
+    assert np.array_equal(idx.cpu().numpy().view(np.uint32), oi) and np.array_equal(D.cpu().numpy(), oD)
+    assert st["tiles_skipped"] > 0.4 * (st["tiles_skipped"] + st["tiles_swept"])
+
+
+def test_other_metrics_need_the_fp32_path(nnm):
+    X = dev(np.zeros((64, 4), np.float32))
+    for p in ("bf16", "fp16", "bf16x3"):
+        with pytest.raises(nnm.NNMError):
+            nnm.nnm_create(X, precision=p, metric="manhattan")
