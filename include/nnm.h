@@ -39,14 +39,15 @@ extern "C" {
 typedef enum {
     NNM_OK = 0,
     NNM_EINVAL = 1,       /* bad argument (sizes, k, restrictions, null pointers)          */
-    NNM_ENONFINITE = 2,   /* X holds NaN or +-Inf ("check correctness of the data array")  */
+    NNM_ENONFINITE = 2,   /* X holds NaN or +-Inf (the main module's data check)           */
     NNM_ENOMEM = 3,       /* device workspace could not be allocated                       */
     NNM_ECUDA = 4,        /* a CUDA runtime call failed                                    */
     NNM_ETIMEOUT = 5,     /* a bounded device-side wait gave up (the context stays usable) */
     NNM_EUNSUPPORTED = 6  /* metric / precision / size not provided by this build          */
 } nnm_status;
 
-/* Eq. (1) is the default; "If it is necessary, other metrics could be chosen".  With
+/* Eq. (1) (Euclidean) is the default; the paper allows another metric where a task
+ * needs one.  With
  * e_k = (double)x_ik - (double)x_jk in feature order, binary64, no contraction:
  *   NNM_EUCLIDEAN  D = sum of e_k^2 (Eq. (1) squared); a merge's length is sqrt(D) and the
  *                  maximum joining distance c admits D <= c*c.
@@ -202,7 +203,7 @@ nnm_status nnm_nearest(nnm_ctx *ctx, int32_t k, uint32_t *idx_dev, double *D_dev
 /* nnm_cluster -- the NNM merge tree (single linkage, minimum spanning tree under
  * key order) and the restricted joins on it.
  *   restrictions  may be NULL (no restriction).  EINVAL: negative values, KL3 <= KL2
- *                 with both set ("Obviously KL3 > KL2"); EUNSUPPORTED: semantics != 0.
+ *                 with both set (the paper takes KL3 above KL2); EUNSUPPORTED: semantics != 0.
  *   merges_dev    nnm_merge [N-1] device, the accepted joins in acceptance order.
  *   n_merges_host receives their number.
  *   labels_dev    int32 [N] device: cluster of every row, 0..K-1, numbered by each

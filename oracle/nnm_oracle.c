@@ -25,8 +25,8 @@
 /* Distance and pair order                                                    */
 /* ------------------------------------------------------------------------- */
 
-/* The metric of every distance below ("If it is necessary, other metrics could be
- * chosen", after Eq. (1)); set once before a computation. */
+/* The metric of every distance below (Eq. (1) is Euclidean; the paper allows another
+ * metric where a task needs one); set once before a computation. */
 static int32_t g_metric = OR_EUCLIDEAN;
 
 void or_set_metric(int32_t metric) { g_metric = metric; }
@@ -650,7 +650,7 @@ int64_t or_restrict_literal(const float *X, int64_t N, int32_t d, const or_restr
 }
 
 /* ------------------------------------------------------------------------- */
-/* Final labels ("Objectives of the main module": final computations)          */
+/* Final labels ("Objectives of the main module": the closing computations)    */
 /* ------------------------------------------------------------------------- */
 
 int64_t or_labels(const or_merge *merges, int64_t m, int64_t N, int32_t *labels_out)

@@ -570,7 +570,7 @@ nnm_status prepare(nnm_ctx *c)
     NNM_CUDA(c, cudaMemsetAsync(c->dstat, 0, 16 * sizeof(unsigned long long), s));
     NNM_CUDA(c, cudaMemsetAsync(c->derr, 0, 4 * sizeof(int), s));
 
-    // "check correctness of the data array"
+    // the main module's data check ("Objectives of the main module")
     NNM_CUDA(c, launch_check_finite(c->X, c->N * c->d, &c->derr[2], s));
     int bad = 0;
     NNM_CUDA(c, cudaMemcpyAsync(&bad, &c->derr[2], sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -2,8 +2,8 @@
 //
 // The second and third parallel items of the paper ("Overall idea of the algorithm":
 // distances between all pairs, then selection of the minimum distances) fused into
-// one pass over row tile x column range, the "two logical blocks of data" of the
-// paper's pair construction.  Each thread owns two rows (registers) and each step
+// one pass over row tile x column range (the paper pairs two blocks of the data in
+// each step of its pair construction).  Each thread owns two rows (registers) and each step
 // evaluates two columns from shared memory (cp.async, double buffered):
 //     s~(i,j) = fl32( sum_k (x_ik - x_jk)^2 ),   k = 0..d-1 in order, one FMA per k.
 // Features beyond d are zero in both operands (adding +0 leaves the sum unchanged), so

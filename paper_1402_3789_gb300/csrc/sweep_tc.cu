@@ -5,7 +5,7 @@
 // B_j = [-2 x_hat_j, a_j, 1,1,1] (prepared by k_tc_operands, K padded to kpad) give
 // |x_hat_i|^2 + |x_hat_j|^2 - 2 x_hat_i.x_hat_j directly in the FP32 accumulator, so
 // the epilogue is a compare against the row's threshold (a 3-input min over 32
-// values, then the rare slow path) -- the fused "distance + minimum selection" of the
+// values, then the rare slow path) -- distances and minimum selection fused, the
 // paper's second and third parallel items.
 //
 // CTA = 256 rows (two M=128 MMAs sharing each B tile) x one column range, 320 threads:

@@ -282,7 +282,7 @@ def test_restrict_none_is_whole_tree(oracle_mod):
 
 def test_restrict_max_join_distance(oracle_mod):
     assert restrict(oracle_mod, LINE, max_join_dist=2.5) == [(0, 1, 1.0, 2), (1, 2, 4.0, 3)]
-    # "greater than the specified one" blocks: equal distance joins
+    # only a distance above the cap blocks: an equal distance joins
     assert restrict(oracle_mod, LINE, max_join_dist=2.0) == [(0, 1, 1.0, 2), (1, 2, 4.0, 3)]
     assert restrict(oracle_mod, LINE, max_join_dist=1.999) == [(0, 1, 1.0, 2)]
 
@@ -432,7 +432,7 @@ def test_labels_partition_and_order(oracle_mod):
 
 
 # ----------------------------------------------------------------------------------
-# other metrics (the paper: "If it is necessary, other metrics could be chosen")
+# other metrics (Eq. 1 is Euclidean; the paper allows another metric where a task needs one)
 # ----------------------------------------------------------------------------------
 
 def metric_by_hand(x, y, metric):
