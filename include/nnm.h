@@ -114,7 +114,7 @@ typedef struct {
     uint32_t a;        /* smaller row index of the joining pair */
     uint32_t b;        /* larger row index */
     double D;          /* D(a,b) */
-    double dist;       /* sqrt(D), correctly rounded */
+    double dist;       /* length: sqrt(D) correctly rounded (Euclidean), D (others) */
     int64_t new_size;  /* rows in the cluster the join forms */
 } nnm_merge;
 
@@ -209,7 +209,9 @@ nnm_status nnm_nearest(nnm_ctx *ctx, int32_t k, uint32_t *idx_dev, double *D_dev
  *   labels_dev    int32 [N] device: cluster of every row, 0..K-1, numbered by each
  *                 cluster's smallest row index.
  *   n_clusters_host  receives K.
- * N >= 2 required. */
+ * N >= 2 required.  Without KL2, KL3 and KL4 the accepted joins are a prefix of the
+ * key-ordered tree and are computed in parallel; the first such call allocates up to
+ * about 220 bytes per tree edge of scratch in the context (kept until nnm_destroy). */
 nnm_status nnm_cluster(nnm_ctx *ctx, const nnm_restrictions *restrictions, nnm_merge *merges_dev,
                        int64_t *n_merges_host, int32_t *labels_dev, int64_t *n_clusters_host);
 

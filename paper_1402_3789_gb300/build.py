@@ -30,6 +30,7 @@ UNITS = [
     ("rounds", "rounds.cu", []),
     ("sort", "sort.cu", []),
     ("restrict", "restrict.cu", []),
+    ("dendro", "dendro.cu", []),
     ("restrict_static", "restrict_static.cu", []),
 ]
 

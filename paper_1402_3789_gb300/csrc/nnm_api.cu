@@ -101,10 +101,15 @@ struct nnm_ctx {
     // restriction walk / labels
     uint32_t *uf_parent = nullptr, *uf_size = nullptr, *deferred = nullptr, *minm = nullptr, *flag = nullptr,
              *block_sums = nullptr;
+    // restriction cut (no size gate): per-instance counts, level state, hash table
+    unsigned long long *cut_cnt = nullptr, *cut_hkey = nullptr;
+    uint32_t *cut_lab = nullptr, *cut_w = nullptr, *cut_slot = nullptr;
+    uint32_t *cut_hpar = nullptr, *cut_hw = nullptr, *cut_hsum = nullptr, *cut_hlab = nullptr;
+    int64_t cut_cap = 0, cut_H = 0;
     // small device block: counters and statistics
     uint32_t *dcount = nullptr;             // [0] ovf, [1..3] round counters, [4] n_edges
     unsigned long long *dstat = nullptr;    // [0] max_abs [1] max_rel [2] pairs [3] max_cand [4] n_merges [5] K [6] maxbits..
-    int *derr = nullptr;                    // [0] sweep time-out, [1] collect retry, [2] non-finite
+    int *derr = nullptr;                    // [0] sweep time-out, [1] collect retry, [2] non-finite, [3] cut union
     // events
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     nnm_stats stats{};
@@ -255,6 +260,24 @@ nnm_status ensure_ovf(nnm_ctx *c, size_t slots)
     NNM_TRY(dalloc(c, &c->coll_cnt, slots));
     NNM_TRY(dalloc(c, &c->slot_thr, slots));
     c->ovf_cap = slots;
+    return NNM_OK;
+}
+
+nnm_status ensure_cut(nnm_ctx *c, int64_t m)
+{
+    if (!c->cut_cnt) NNM_TRY(dalloc(c, &c->cut_cnt, (size_t)c->n_inst + 1));
+    if (m <= c->cut_cap) return NNM_OK;
+    const int64_t H = cut_hash_slots(m);
+    NNM_TRY(dalloc(c, &c->cut_lab, (size_t)(2 * m)));
+    NNM_TRY(dalloc(c, &c->cut_w, (size_t)(2 * m)));
+    NNM_TRY(dalloc(c, &c->cut_slot, (size_t)(2 * m)));
+    NNM_TRY(dalloc(c, &c->cut_hkey, (size_t)H));
+    NNM_TRY(dalloc(c, &c->cut_hpar, (size_t)H));
+    NNM_TRY(dalloc(c, &c->cut_hw, (size_t)H));
+    NNM_TRY(dalloc(c, &c->cut_hsum, (size_t)H));
+    NNM_TRY(dalloc(c, &c->cut_hlab, (size_t)H));
+    c->cut_cap = m;
+    c->cut_H = H;
     return NNM_OK;
 }
 
@@ -1073,7 +1096,40 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
     {
         Phase total(c, &c->stats.ms_total);
         NNM_TRY(build_tree(c, c->opt.freeze_at_cap ? cap2 : INFINITY));
-        {
+        const bool size_gates = r.kl2_max_pre_size > 0 || r.kl3_max_size > 0 || r.kl4_min_size > 0;
+        int64_t n_cut = 0;
+        if (!size_gates) {
+            // only the cap and KL1: a parallel cut, new sizes by halving rank ranges
+            Phase ph(c, &c->stats.ms_restrict);
+            NNM_TRY(ensure_cut(c, c->n_tree));
+            CutArgs ca{};
+            ca.edges = c->tree;
+            ca.m = c->n_tree;
+            ca.N = c->N;
+            ca.cap2 = cap2;
+            ca.kl1 = r.kl1_stop_clusters;
+            ca.metric = c->metric;
+            ca.n_inst = c->n_inst;
+            ca.inst_off = c->inst_off;
+            ca.ebeg = c->ebeg;
+            ca.eend = c->eend;
+            ca.inst_of_row = c->inst_pos;
+            ca.merges = merges_dev;
+            ca.n_merges = &c->dstat[4];
+            ca.uf_parent = c->uf_parent;
+            ca.err_flag = &c->derr[3];
+            ca.cnt = c->cut_cnt;
+            ca.lab = c->cut_lab;
+            ca.w = c->cut_w;
+            ca.slot = c->cut_slot;
+            ca.hkey = c->cut_hkey;
+            ca.hpar = c->cut_hpar;
+            ca.hw = c->cut_hw;
+            ca.hsum = c->cut_hsum;
+            ca.hlab = c->cut_hlab;
+            ca.H = c->cut_H;
+            NNM_CUDA(c, launch_restrict_cut(ca, &n_cut, c->stream));
+        } else {
             Phase ph(c, &c->stats.ms_restrict);
             RestrictArgs ra{};
             ra.edges = c->tree;
@@ -1113,8 +1169,14 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
         }
     }
     unsigned long long h[2];
+    int uf_err = 0;
     NNM_CUDA(c, cudaMemcpyAsync(h, &c->dstat[4], sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    NNM_CUDA(c, cudaMemcpyAsync(&uf_err, &c->derr[3], sizeof uf_err, cudaMemcpyDeviceToHost, c->stream));
     NNM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (uf_err) {
+        NNM_CUDA(c, cudaMemsetAsync(&c->derr[3], 0, sizeof(int), c->stream));
+        return fail(c, NNM_ECUDA, "a union-find join in the restriction cut gave up");
+    }
     *n_merges_host = (int64_t)h[0];
     *n_clusters_host = (int64_t)h[1];
     return read_stats(c);
@@ -1156,6 +1218,15 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->eend);
     dfree(c->inst_nm);
     dfree(c->merges_tmp);
+    dfree(c->cut_cnt);
+    dfree(c->cut_lab);
+    dfree(c->cut_w);
+    dfree(c->cut_slot);
+    dfree(c->cut_hkey);
+    dfree(c->cut_hpar);
+    dfree(c->cut_hw);
+    dfree(c->cut_hsum);
+    dfree(c->cut_hlab);
     dfree(c->blk_c);
     dfree(c->blk_rho);
     dfree(c->mu_f);

@@ -383,6 +383,35 @@ cudaError_t launch_restrict(const RestrictArgs &a, cudaStream_t s);
 cudaError_t launch_edge_ranges(const nnm_edge *edges, int64_t m, const uint32_t *inst_of_row, int64_t n_inst,
                                int64_t *ebeg, int64_t *eend, cudaStream_t s);
 
+// Restriction step when no gate reads cluster sizes (cap and KL1 only): a parallel
+// cut of each instance's key-ordered edges and the new sizes by halving rank ranges
+// (dendro.cu).  Instances as in RestrictArgs.
+struct CutArgs {
+    const nnm_edge *edges;     // tree edges sorted by (instance, key)
+    int64_t m;
+    int64_t N;
+    double cap2;               // inf: none
+    int64_t kl1;
+    int metric;
+    int64_t n_inst;
+    const int64_t *inst_off, *ebeg, *eend;   // batched only
+    const uint32_t *inst_of_row;             // batched only
+    nnm_merge *merges;         // [m] out: the accepted joins, (instance, key) order
+    unsigned long long *n_merges;   // device out
+    uint32_t *uf_parent;       // [N] out: a union-find of the final clusters
+    int *err_flag;             // set if a union gave up (never expected)
+    // scratch
+    unsigned long long *cnt;   // [n_inst + 1]
+    uint32_t *lab, *w, *slot;  // [2m] each
+    unsigned long long *hkey;  // [H]
+    uint32_t *hpar, *hw, *hsum, *hlab;   // [H]
+    int64_t H;                 // cut_hash_slots(m)
+};
+
+int64_t cut_hash_slots(int64_t m);
+// Returns after one synchronisation (the accepted count decides the levels).
+cudaError_t launch_restrict_cut(const CutArgs &a, int64_t *n_merges_host, cudaStream_t s);
+
 struct LabelArgs {
     int64_t N;
     uint32_t *uf_parent;       // union-find after the restriction walk

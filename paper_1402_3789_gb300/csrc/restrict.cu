@@ -1,7 +1,9 @@
 // restrict.cu -- K7 restriction walk and K8 labels.
 //
 // The restrictions of "Problem statement" and "Problem settings" (maximum joining
-// distance, KL1..KL4) act on the merge sequence: the tree edges are walked in key order
+// distance, KL1..KL4) act on the merge sequence.  With only the cap and KL1 the accepted
+// joins are a prefix and dendro.cu computes them in parallel; when KL2, KL3 or KL4 is
+// set (gates that read cluster sizes) the tree edges are walked in key order
 // (in a batched context: each instance's edges, one CTA per instance, in parallel)
 // with a union-find that tracks cluster sizes and the cluster count.  The walk is
 // sequential by definition (each decision reads sizes that earlier joins changed), so

@@ -184,6 +184,35 @@ def test_cluster_ragged_and_tiny(nnm, orc, precision):
         assert np.array_equal(merges, omerges) and K == oK and np.array_equal(labels, olabels)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16x3"])
+def test_cluster_cut_chains_and_extremes(nnm, orc, precision):
+    """The cap/KL1-only restriction step (a cut plus new sizes by halving rank ranges)
+    on the shapes that make a dendrogram deep: rows on a line with growing gaps (each
+    join adds one row to one cluster: new sizes 2..N), a growing spiral, all rows equal,
+    and restrictions that admit nothing, everything, or stop at KL1 = N - 1."""
+    rng = np.random.default_rng(17)
+    n = 3000
+    line = np.zeros((n, 3), np.float32)
+    line[:, 0] = np.cumsum(np.linspace(0.01, 1.0, n)).astype(np.float32)
+    line = line[rng.permutation(n)]
+    t = np.linspace(0, 40, 2500)
+    spiral = np.stack([t * np.cos(t), t * np.sin(t), 0.1 * t], 1).astype(np.float32)
+    same = np.ones((700, 5), np.float32)
+    cases = [(line, None), (line, {"kl1_stop_clusters": 100}), (line, {"max_join_dist": 1e-9}),
+             (line, {"kl1_stop_clusters": n - 1}), (line, {"kl1_stop_clusters": n + 5}),
+             (spiral, None), (spiral, {"max_join_dist": 0.5, "kl1_stop_clusters": 3}),
+             (same, None), (same, {"kl1_stop_clusters": 2})]
+    for i, (X, restr) in enumerate(cases):
+        tree, merges, labels, K, _ = run_cluster(nnm, X, restr, precision)
+        otree, omerges, olabels, oK = orc.cluster(X, restr)
+        assert np.array_equal(tree, otree), i
+        assert np.array_equal(merges, omerges), i
+        assert K == oK and np.array_equal(labels, olabels), i
+    # the line's dendrogram is one chain: every join grows the same cluster
+    _, merges, _, _, _ = run_cluster(nnm, line, None, precision)
+    assert np.array_equal(np.sort(merges["new_size"]), np.arange(2, n + 1))
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_cluster_freeze_at_cap_keeps_the_restricted_result(nnm, orc, precision):
     X = make("nnm_n262144_d16", 8000)
@@ -295,9 +324,10 @@ def batched_cases():
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("restr", [{}, {"max_join_dist": 1.2}, {"kl4_min_size": 5, "kl3_max_size": 400},
+@pytest.mark.parametrize("restr", [{}, {"max_join_dist": 1.2}, {"kl1_stop_clusters": 4},
+                                   {"kl4_min_size": 5, "kl3_max_size": 400},
                                    {"kl1_stop_clusters": 3, "kl2_max_pre_size": 150}],
-                         ids=["none", "cap", "kl4kl3", "kl1kl2"])
+                         ids=["none", "cap", "kl1", "kl4kl3", "kl1kl2"])
 def test_batched_context_equals_each_instance_alone(nnm, orc, precision, restr):
     inst = batched_cases()
     ctx = nnm.nnm_create_batched([dev(x) for x in inst], precision=precision)
