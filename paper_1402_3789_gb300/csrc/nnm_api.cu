@@ -59,6 +59,10 @@ struct nnm_ctx {
     unsigned long long *inst_nm = nullptr;      // merges per instance (restriction walks)
     nnm_merge *merges_tmp = nullptr;
     float *tile_c = nullptr, *tile_rho = nullptr, *mu_f = nullptr, *blk_c = nullptr, *blk_rho = nullptr;
+    // landmark bounds: per row the FP32 squared distance to its nearest landmark (x units),
+    // per position an upper bound of that distance and per tile / block a lower bound of
+    // its columns' distances to any landmark (y units)
+    float *land_d2 = nullptr, *lup = nullptr, *tile_lmin = nullptr, *blk_lmin = nullptr;
     int tile_w = 0;
     float lb_R2 = 0.f, lb_eps = 0.f, lb_gamma = 0.f;
     // operands
@@ -322,6 +326,9 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.tile_w = c->tile_w;
     a.tile_c = c->tile_c;
     a.tile_rho = c->tile_rho;
+    a.lup = c->lup;
+    a.tile_lmin = c->tile_lmin;
+    a.blk_lmin = c->blk_lmin;
     a.group = c->group;
     a.metric = c->metric;
     a.inst_pos = c->inst_pos;
@@ -626,7 +633,6 @@ nnm_status prepare(nnm_ctx *c)
             cudaFree(lrank);
             cudaFree(rarg);
             cudaFree(ldist);
-            cudaFree(rdist);
             cudaFree(tau);
             cudaFree(hist);
         };
@@ -642,7 +648,8 @@ nnm_status prepare(nnm_ctx *c)
             if ((st = dalloc(c, &lrank, (size_t)L)) != NNM_OK) break;
             if ((st = dalloc(c, &ldist, (size_t)L)) != NNM_OK) break;
             if ((st = dalloc(c, &rarg, (size_t)c->N)) != NNM_OK) break;
-            if ((st = dalloc(c, &rdist, (size_t)c->N)) != NNM_OK) break;
+            if ((st = dalloc(c, &c->land_d2, (size_t)c->N)) != NNM_OK) break;
+            rdist = c->land_d2;   // kept for the landmark bounds of the tiles
             if ((st = dalloc(c, &tau, 1)) != NNM_OK) break;
             if ((st = dalloc(c, &hist, 4096)) != NNM_OK) break;
         } while (0);
@@ -742,12 +749,20 @@ nnm_status prepare(nnm_ctx *c)
         const int64_t nt = (c->N + c->tile_w - 1) / c->tile_w;
         NNM_TRY(dalloc(c, &c->tile_c, (size_t)nt * 2 * c->d));
         NNM_TRY(dalloc(c, &c->tile_rho, (size_t)nt * 2));
+        // landmark bounds: y = x exactly on the FP32 path; on the tensor path the rounding
+        // of y = (x - mu) * scale moves a distance by at most 2^-23 of the largest |y|
+        // (<= Pmax + R), far inside the slack
+        const float land_slack = is_tensor(c) ? up_f((c->margin.Pmax + c->margin.R) * 0x1p-12 * (1.0 + 0x1p-10)) : 0.0f;
+        NNM_TRY(dalloc(c, &c->lup, (size_t)c->N));
+        NNM_TRY(dalloc(c, &c->tile_lmin, (size_t)nt));
         NNM_CUDA(c, launch_tile_spheres(c->X, c->N, c->d, c->pos2row, c->group, c->mu_f, (float)c->scale, c->tile_w,
-                                        c->tile_c, c->tile_rho, s));
+                                        c->tile_c, c->tile_rho, c->land_d2, land_slack, c->lup, c->tile_lmin, s));
         const int64_t nb = (nt + 31) / 32;
         NNM_TRY(dalloc(c, &c->blk_c, (size_t)nb * c->d));
         NNM_TRY(dalloc(c, &c->blk_rho, (size_t)nb));
-        NNM_CUDA(c, launch_block_spheres(c->tile_c, c->tile_rho, nt, c->d, c->blk_c, c->blk_rho, s));
+        NNM_TRY(dalloc(c, &c->blk_lmin, (size_t)nb));
+        NNM_CUDA(c, launch_block_spheres(c->tile_c, c->tile_rho, nt, c->d, c->blk_c, c->blk_rho, c->tile_lmin,
+                                         c->blk_lmin, s));
         const double grow = 1.0 + 0x1p-20;
         if (is_tensor(c)) {
             c->lb_R2 = up_f(2.0 * c->margin.R * grow);
@@ -1211,6 +1226,10 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->pos2row);
     dfree(c->tile_c);
     dfree(c->tile_rho);
+    dfree(c->land_d2);
+    dfree(c->lup);
+    dfree(c->tile_lmin);
+    dfree(c->blk_lmin);
     dfree(c->group);
     dfree(c->inst_off);
     dfree(c->inst_pos);

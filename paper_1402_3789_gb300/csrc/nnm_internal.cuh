@@ -126,6 +126,11 @@ struct SweepArgs {
     const uint32_t *group;    // [N] landmark group of each position (row tiles split alike)
     const float *blk_c;       // tensor path: [nblocks][d] sphere of each block of 32 tiles
     const float *blk_rho;     // [nblocks]
+    // landmark bounds (triangle inequality through the landmark of a row): every pair
+    // (i, j) has |y_i - y_j| >= lmin(j) - lup(i)
+    const float *lup;         // [N] per position: upper bound on |y - y_l|, l its landmark
+    const float *tile_lmin;   // [ntiles] lower bound on every column's distance to any landmark
+    const float *blk_lmin;    // tensor path: [nblocks] the same over each block of 32 tiles
     const float *mu_f;        // [d] (nullptr: 0)
     float scale_f;
     float lb_R2;              // tensor: 2 * max rounding radius (scaled); FP32: 0
@@ -151,6 +156,32 @@ __device__ __forceinline__ float sphere_slack(float rho, float ymax)
 // Other metrics (FP32 path only): the Euclidean gap bounds them too, since
 // |v|_1 >= |v|_2 and |v|_inf >= |v|_2 / sqrt(d); the candidate value is then the gap
 // (Manhattan) or gap / sqrt(d) (Chebyshev) instead of its square.
+// The bound from dist, a lower bound of the centre distance.
+__device__ __forceinline__ float dist_lower_bound(float dist, float rhoR, float rhoC, int d, float lb_R2,
+                                                  float lb_eps, float lb_gamma, int metric = 0)
+{
+    const float gap = dist - rhoR - rhoC - lb_R2;
+    if (!(gap > 0.0f)) return -INFINITY;
+    const float sq = metric == 0 ? gap * gap * (1.0f - 0x1p-12f)
+                     : (metric == 1 ? gap : gap * rsqrtf((float)d) * (1.0f - 0x1p-12f));
+    return sq * (1.0f - lb_gamma) - lb_eps;
+}
+
+// The bound from s = the FP32 sum of (cR_k - cC_k)^2 (the squared centre distance).
+__device__ __forceinline__ float gap_lower_bound(float s, float rhoR, float rhoC, int d, float lb_R2, float lb_eps,
+                                                 float lb_gamma, int metric = 0)
+{
+    return dist_lower_bound(sqrtf(s) * (1.0f - 0x1p-12f), rhoR, rhoC, d, lb_R2, lb_eps, lb_gamma, metric);
+}
+
+// Landmark bound: every column j of a tile has |y_j - y_l| >= lmin for every landmark l,
+// and every row i of a part has |y_i - y_l(i)| <= dmax, so |y_i - y_j| >= lmin - dmax.
+__device__ __forceinline__ float land_lower_bound(float lmin, float dmax, int d, float lb_R2, float lb_eps,
+                                                  float lb_gamma, int metric = 0)
+{
+    return dist_lower_bound(lmin, dmax, 0.0f, d, lb_R2, lb_eps, lb_gamma, metric);
+}
+
 __device__ __forceinline__ float tile_lower_bound(const float *cR, float rhoR, const float *cC, float rhoC, int d,
                                                   float lb_R2, float lb_eps, float lb_gamma, int metric = 0)
 {
@@ -166,12 +197,7 @@ __device__ __forceinline__ float tile_lower_bound(const float *cR, float rhoR, c
             s = fmaf(e, e, s);
         }
     }
-    const float dist = sqrtf(s) * (1.0f - 0x1p-12f);
-    const float gap = dist - rhoR - rhoC - lb_R2;
-    if (!(gap > 0.0f)) return -INFINITY;
-    const float sq = metric == 0 ? gap * gap * (1.0f - 0x1p-12f)
-                     : (metric == 1 ? gap : gap * rsqrtf((float)d) * (1.0f - 0x1p-12f));
-    return sq * (1.0f - lb_gamma) - lb_eps;
+    return gap_lower_bound(s, rhoR, rhoC, d, lb_R2, lb_eps, lb_gamma, metric);
 }
 
 // Launch the FP32 direct sweep (template on d).
@@ -288,10 +314,13 @@ cudaError_t launch_max_sqnorm(const float *X, int64_t N, int d, const double *mu
 // Bounding spheres of the column tiles (tile_w consecutive positions).
 // Bounding spheres of blocks of 32 consecutive tiles, from the tiles' two spheres each.
 cudaError_t launch_block_spheres(const float *tile_c, const float *tile_rho, int64_t ntiles, int d, float *blk_c,
-                                 float *blk_rho, cudaStream_t s);
+                                 float *blk_rho, const float *tile_lmin, float *blk_lmin, cudaStream_t s);
+// With land_d2 (per row: FP32 squared distance to the nearest landmark, x units), also
+// lup [N] and tile_lmin [ntiles] in y units (scale_f times x units, plus land_slack for
+// the rounding of y = (x - mu) * scale).
 cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const uint32_t *group,
                                 const float *mu_f, float scale_f, int tile_w, float *tile_c, float *tile_rho,
-                                cudaStream_t s);
+                                const float *land_d2, float land_slack, float *lup, float *tile_lmin, cudaStream_t s);
 cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale,
                                int fp16, int terms, int kpad, int64_t Npad, const uint32_t *row2pos, uint16_t *XA,
                                uint16_t *XB,

@@ -421,7 +421,9 @@ __global__ void __launch_bounds__(128) k_tile_spheres(const float *__restrict__ 
                                                       const uint32_t *__restrict__ pos2row,
                                                       const uint32_t *__restrict__ group,
                                                       const float *__restrict__ mu_f, float scale_f, int tile_w,
-                                                      float *__restrict__ tile_c, float *__restrict__ tile_rho)
+                                                      float *__restrict__ tile_c, float *__restrict__ tile_rho,
+                                                      const float *__restrict__ land_d2, float land_slack,
+                                                      float *__restrict__ lup, float *__restrict__ tile_lmin)
 {
     __shared__ float csum[2][32];
     __shared__ unsigned int rbits[2], ybits;
@@ -453,6 +455,21 @@ __global__ void __launch_bounds__(128) k_tile_spheres(const float *__restrict__ 
         atomicAdd(&cnt[h], 1);
         atomicMax(&ybits, __float_as_uint(sqrtf(ny)));
     }
+    // Landmark distances in y units.  a = sqrtf(FP32 squared distance) is within 2^-20 of
+    // the exact x distance to the row's landmark, and the FP32 nearest-landmark search
+    // compared every landmark, so a also bounds the distance to any landmark from below
+    // within the same factor; scale_f is a power of two, and land_slack covers the
+    // rounding of y = (x - mu) * scale.  Up: |y - y_l| <= lup; down: every landmark is at
+    // least lo away.
+    __shared__ unsigned int lmin_bits;
+    if (threadIdx.x == 0) lmin_bits = 0x7F800000u;   // +inf
+    __syncthreads();
+    if (land_d2 && valid) {
+        const float a = sqrtf(land_d2[pos2row[p]]) * scale_f;
+        lup[p] = __fadd_ru(__fmul_ru(a, 1.0f + 0x1p-12f), land_slack);
+        const float lo = fmaxf(__fsub_rd(__fmul_rd(a, 1.0f - 0x1p-12f), land_slack), 0.0f);
+        atomicMin(&lmin_bits, __float_as_uint(lo));   // non-negative floats order as their bits
+    }
     __syncthreads();
     float dd = 0.0f;
 #pragma unroll
@@ -471,14 +488,16 @@ __global__ void __launch_bounds__(128) k_tile_spheres(const float *__restrict__ 
     if (threadIdx.x < 2)
         tile_rho[blockIdx.x * 2 + threadIdx.x] =
             cnt[threadIdx.x] > 0 ? sphere_slack(__uint_as_float(rbits[threadIdx.x]), __uint_as_float(ybits)) : -1.0f;
+    if (land_d2 && threadIdx.x == 0) tile_lmin[blockIdx.x] = __uint_as_float(lmin_bits);
 }
 
 cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t *pos2row, const uint32_t *group,
                                 const float *mu_f, float scale_f, int tile_w, float *tile_c, float *tile_rho,
-                                cudaStream_t s)
+                                const float *land_d2, float land_slack, float *lup, float *tile_lmin, cudaStream_t s)
 {
     const int64_t nt = (N + tile_w - 1) / tile_w;
-    k_tile_spheres<<<(unsigned)nt, 128, 0, s>>>(X, N, d, pos2row, group, mu_f, scale_f, tile_w, tile_c, tile_rho);
+    k_tile_spheres<<<(unsigned)nt, 128, 0, s>>>(X, N, d, pos2row, group, mu_f, scale_f, tile_w, tile_c, tile_rho,
+                                                 land_d2, land_slack, lup, tile_lmin);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -488,10 +507,12 @@ cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t
 // |c - centre| + rho over them, enlarged by sphere_slack: a sphere holding all of them.
 __global__ void __launch_bounds__(64) k_block_spheres(const float *__restrict__ tile_c,
                                                      const float *__restrict__ tile_rho, int64_t ntiles, int d,
-                                                     float *__restrict__ blk_c, float *__restrict__ blk_rho)
+                                                     float *__restrict__ blk_c, float *__restrict__ blk_rho,
+                                                     const float *__restrict__ tile_lmin,
+                                                     float *__restrict__ blk_lmin)
 {
     __shared__ float csum[32];
-    __shared__ unsigned int rbits, ybits;
+    __shared__ unsigned int rbits, ybits, lbits;
     __shared__ int cnt;
     const int64_t sp = (int64_t)blockIdx.x * 64 + threadIdx.x;   // sphere index: tile * 2 + part
     const bool valid = sp < ntiles * 2 && tile_rho[sp] >= 0.0f;
@@ -499,9 +520,11 @@ __global__ void __launch_bounds__(64) k_block_spheres(const float *__restrict__ 
     if (threadIdx.x == 0) {
         rbits = 0u;
         ybits = 0u;
+        lbits = 0x7F800000u;
         cnt = 0;
     }
     __syncthreads();
+    if (tile_lmin && (sp & 1) == 0 && sp < ntiles * 2) atomicMin(&lbits, __float_as_uint(tile_lmin[sp >> 1]));
     float c[32];
     float nc = 0.0f;
 #pragma unroll
@@ -529,13 +552,14 @@ __global__ void __launch_bounds__(64) k_block_spheres(const float *__restrict__ 
     __syncthreads();
     if (threadIdx.x < d) blk_c[(int64_t)blockIdx.x * d + threadIdx.x] = csum[threadIdx.x] / (float)(cnt > 0 ? cnt : 1);
     if (threadIdx.x == 0) blk_rho[blockIdx.x] = cnt > 0 ? sphere_slack(__uint_as_float(rbits), __uint_as_float(ybits)) : -1.0f;
+    if (tile_lmin && threadIdx.x == 0) blk_lmin[blockIdx.x] = __uint_as_float(lbits);
 }
 
 cudaError_t launch_block_spheres(const float *tile_c, const float *tile_rho, int64_t ntiles, int d, float *blk_c,
-                                 float *blk_rho, cudaStream_t s)
+                                 float *blk_rho, const float *tile_lmin, float *blk_lmin, cudaStream_t s)
 {
     const int64_t nb = (ntiles + 31) / 32;
-    k_block_spheres<<<(unsigned)nb, 64, 0, s>>>(tile_c, tile_rho, ntiles, d, blk_c, blk_rho);
+    k_block_spheres<<<(unsigned)nb, 64, 0, s>>>(tile_c, tile_rho, ntiles, d, blk_c, blk_rho, tile_lmin, blk_lmin);
     count_launches(1);
     return cudaGetLastError();
 }

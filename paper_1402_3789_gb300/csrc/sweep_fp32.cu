@@ -100,11 +100,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     // in two parts, the rows of the first landmark group and the rest, and each part's
     // largest row threshold after each tile.
     __shared__ float cR[2][32], wthr[2][kThreads / 32], blk_thr[2];
-    __shared__ unsigned int rho_bits[2], ymax_bits, cmin, cmax;
+    __shared__ unsigned int rho_bits[2], ymax_bits, cmin, cmax, lup_bits[2];
     __shared__ int nvalid[2];
     if (t < 64) (&cR[0][0])[t] = 0.0f;
     if (t == 0) {
         rho_bits[0] = rho_bits[1] = 0u;
+        lup_bits[0] = lup_bits[1] = 0u;
         ymax_bits = 0u;
         nvalid[0] = nvalid[1] = 0;
         blk_thr[0] = blk_thr[1] = INFINITY;
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
             }
             atomicAdd(&nvalid[part[r]], 1);
             atomicMax(&ymax_bits, __float_as_uint(sqrtf(ny)));
+            if (a.lup) atomicMax(&lup_bits[part[r]], __float_as_uint(a.lup[row[r]]));
         }
         __syncthreads();
 #pragma unroll
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             lb[h] = INFINITY;
-                            if (rhoR[h] >= 0.0f)
+                            if (rhoR[h] >= 0.0f) {
                                 for (int hc = 0; hc < 2; ++hc) {
                                     const float rc = a.tile_rho[ct * 2 + hc];
                                     if (rc >= 0.0f)
@@ -192,6 +194,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
                                                                               rc, a.d, 0.0f, a.lb_eps, a.lb_gamma,
                                                                               a.metric));
                                 }
+                                // the landmark bound of the tile (see tile_lower_bound's notes on metrics)
+                                if (a.lup && a.tile_lmin[ct] > 0.0f)
+                                    lb[h] = fmaxf(lb[h], land_lower_bound(a.tile_lmin[ct], __uint_as_float(lup_bits[h]),
+                                                                          a.d, 0.0f, a.lb_eps, a.lb_gamma, a.metric));
+                            }
                         }
                     }
                 }

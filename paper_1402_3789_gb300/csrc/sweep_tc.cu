@@ -205,7 +205,8 @@ struct __align__(8) TcShared {
     int npub;                    // epilogue warps that have published a threshold
     int plan_ct[kPlanQ];         // planned column tiles (-1: end), a ring of kPlanQ ...
     unsigned int plan_mask[kPlanQ];   // ... with the epilogue warps that need them
-    int plan_head, plan_tail;    // entries written by the planner / taken by the producer
+    int plan_head, plan_tail;
+    unsigned int lup_bits[2];    // largest landmark distance bound of each row part    // entries written by the planner / taken by the producer
     unsigned int cmin, cmax;     // smallest and largest component among the tile's rows
 };
 constexpr int kShBytes = 3072;
@@ -283,6 +284,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         for (int w = 0; w < kEpiWarps; ++w) sh->warp_thr[w] = INFINITY;
         for (int k = 0; k < 32; ++k) sh->cR[0][k] = sh->cR[1][k] = 0.0f;
         sh->rho_bits[0] = sh->rho_bits[1] = 0u;
+        sh->lup_bits[0] = sh->lup_bits[1] = 0u;
         sh->ymax_bits = 0u;
         sh->nvalid[0] = sh->nvalid[1] = 0;
         sh->warps_in[0] = sh->warps_in[1] = 0u;
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             atomicAdd(&sh->nvalid[part], 1);
             atomicMax(&sh->ymax_bits, __float_as_uint(sqrtf(ny)));
+            if (a.lup) atomicMax(&sh->lup_bits[part], __float_as_uint(a.lup[myrow]));
         }
         const unsigned int in0 = __ballot_sync(0xffffffffu, myrow_slot >= 0 && part == 0);
         const unsigned int in1 = __ballot_sync(0xffffffffu, myrow_slot >= 0 && part == 1);
@@ -485,6 +488,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             return m;
         };
+        // landmark bound of a column tile or block (lmin) for the two row parts
+        float dmaxR[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) dmaxR[h] = (a.lup && sh->nvalid[h] > 0) ? __uint_as_float(sh->lup_bits[h]) : -1.0f;
+        auto land_bounds = [&](float lmin, float &lb0, float &lb1) {
+            if (!(lmin > 0.0f)) return;
+            if (dmaxR[0] >= 0.0f) lb0 = fmaxf(lb0, land_lower_bound(lmin, dmaxR[0], a.d, a.lb_R2, a.lb_eps, a.lb_gamma));
+            if (dmaxR[1] >= 0.0f) lb1 = fmaxf(lb1, land_lower_bound(lmin, dmaxR[1], a.d, a.lb_R2, a.lb_eps, a.lb_gamma));
+        };
         auto part_bounds = [&](const float *cC, float rhoC, float &lb0, float &lb1) {
             lb0 = rhoR[0] >= 0.0f && rhoC >= 0.0f
                       ? tile_lower_bound(sh->cR[0], rhoR[0], cC, rhoC, a.d, a.lb_R2, a.lb_eps, a.lb_gamma)
@@ -521,6 +533,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 const int cb = blk_at(u0 + lane);
                 float lb0, lb1;
                 part_bounds(a.blk_c + (int64_t)cb * a.d, a.blk_rho[cb], lb0, lb1);
+                if (a.blk_lmin) land_bounds(a.blk_lmin[cb], lb0, lb1);
                 bneed = need_mask(lb0, lb1) != 0u;
             }
             unsigned int bm = __ballot_sync(0xffffffffu, bneed);
@@ -543,6 +556,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                             lb0 = fminf(lb0, l0);
                             lb1 = fminf(lb1, l1);
                         }
+                        if (a.tile_lmin) land_bounds(a.tile_lmin[ct], lb0, lb1);
                         wmask = need_mask(lb0, lb1);
                     }
                 }
