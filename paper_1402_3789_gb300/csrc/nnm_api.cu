@@ -709,7 +709,7 @@ nnm_status prepare(nnm_ctx *c)
         NNM_TRY(dalloc(c, &c->r, (size_t)c->Npad));
         NNM_TRY(dalloc(c, &c->P, (size_t)c->Npad));
         NNM_TRY(dalloc(c, &c->E, (size_t)c->Npad));
-        NNM_CUDA(c, launch_tc_operands(c->X, c->N, c->d, mu, c->scale, c->fp16, c->terms, c->kpad, c->Npad, c->row2pos, c->XA,
+        NNM_CUDA(c, launch_tc_operands(c->X, c->N, c->d, mu, c->scale, c->fp16, c->terms, c->kpad, c->Npad, c->pos2row, c->XA,
                                        c->XB, c->r, c->P, c->E, &c->dstat[9], s));
         unsigned long long mx[3];
         NNM_CUDA(c, cudaMemcpyAsync(mx, &c->dstat[9], sizeof mx, cudaMemcpyDeviceToHost, s));

@@ -322,7 +322,7 @@ cudaError_t launch_tile_spheres(const float *X, int64_t N, int d, const uint32_t
                                 const float *mu_f, float scale_f, int tile_w, float *tile_c, float *tile_rho,
                                 const float *land_d2, float land_slack, float *lup, float *tile_lmin, cudaStream_t s);
 cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale,
-                               int fp16, int terms, int kpad, int64_t Npad, const uint32_t *row2pos, uint16_t *XA,
+                               int fp16, int terms, int kpad, int64_t Npad, const uint32_t *pos2row, uint16_t *XA,
                                uint16_t *XB,
                                float *r, float *P, float *E, unsigned long long *max_bits /*[3]*/,
                                cudaStream_t s);

@@ -119,51 +119,83 @@ cudaError_t launch_landmark_chain(const float *X, int64_t N, int d, int64_t L, u
 }
 
 // For each query q < Q (row q*N/Q of X) the nearest of the R reference rows (row r*N/R)
-// by FP32 squared distance (first one on ties): index and value.
+// by FP32 squared distance (first one on ties): index and value.  Features are summed in
+// order with one FMA each; DP = d rounded up to 4 (the padding adds 0 * 0, which changes
+// no sum).  Each thread takes two queries, so every float4 of a reference row read from
+// shared memory feeds eight FMAs.
+template <int DP>
 __global__ void __launch_bounds__(256) k_nearest_ref(const float *__restrict__ X, int64_t N, int d, int64_t Q,
                                                      int64_t R, uint32_t *__restrict__ arg_out,
                                                      float *__restrict__ dist_out)
 {
-    __shared__ __align__(16) float lm[kLandChunk * 32];
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t row = q < Q ? q * N / Q : 0;
-    float x[32];
+    __shared__ __align__(16) float lm[kLandChunk * DP];
+    const int64_t qa = (int64_t)blockIdx.x * 512 + threadIdx.x, qb = qa + 256;
+    const int64_t ra = qa < Q ? qa * N / Q : 0, rb = qb < Q ? qb * N / Q : 0;
+    float xa[DP], xb[DP];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) x[k] = (q < Q && k < d) ? X[row * d + k] : 0.0f;
-    float best = INFINITY;
-    int64_t arg = 0;
+    for (int k = 0; k < DP; ++k) {
+        xa[k] = k < d ? X[ra * d + k] : 0.0f;
+        xb[k] = k < d ? X[rb * d + k] : 0.0f;
+    }
+    float besta = INFINITY, bestb = INFINITY;
+    int64_t arga = 0, argb = 0;
     for (int64_t m0 = 0; m0 < R; m0 += kLandChunk) {
         __syncthreads();
-        for (int t = threadIdx.x; t < kLandChunk * 32; t += blockDim.x) {
-            const int64_t m = m0 + t / 32;
-            const int k = t % 32;
+        for (int t = threadIdx.x; t < kLandChunk * DP; t += blockDim.x) {
+            const int64_t m = m0 + t / DP;
+            const int k = t % DP;
             lm[t] = (m < R && k < d) ? X[(m * N / R) * d + k] : 0.0f;
         }
         __syncthreads();
-        const int64_t cnt = R - m0 < kLandChunk ? R - m0 : kLandChunk;
+        const int cnt = (int)(R - m0 < kLandChunk ? R - m0 : kLandChunk);
         for (int m = 0; m < cnt; ++m) {
-            float acc = 0.0f;
+            const float4 *l4 = reinterpret_cast<const float4 *>(lm + m * DP);
+            float acca = 0.0f, accb = 0.0f;
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const float e = x[k] - lm[m * 32 + k];
-                acc = fmaf(e, e, acc);
+            for (int k4 = 0; k4 < DP / 4; ++k4) {
+                const float4 v = l4[k4];
+                const float l[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float ea = xa[4 * k4 + j] - l[j], eb = xb[4 * k4 + j] - l[j];
+                    acca = fmaf(ea, ea, acca);
+                    accb = fmaf(eb, eb, accb);
+                }
             }
-            if (acc < best) {
-                best = acc;
-                arg = m0 + m;
+            if (acca < besta) {
+                besta = acca;
+                arga = m0 + m;
+            }
+            if (accb < bestb) {
+                bestb = accb;
+                argb = m0 + m;
             }
         }
     }
-    if (q < Q) {
-        arg_out[q] = (uint32_t)arg;
-        dist_out[q] = best;
+    if (qa < Q) {
+        arg_out[qa] = (uint32_t)arga;
+        dist_out[qa] = besta;
+    }
+    if (qb < Q) {
+        arg_out[qb] = (uint32_t)argb;
+        dist_out[qb] = bestb;
     }
 }
 
 cudaError_t launch_nearest_ref(const float *X, int64_t N, int d, int64_t Q, int64_t R, uint32_t *arg, float *dist,
                                cudaStream_t s)
 {
-    k_nearest_ref<<<(unsigned)((Q + 255) / 256), 256, 0, s>>>(X, N, d, Q, R, arg, dist);
+    const unsigned blocks = (unsigned)((Q + 511) / 512);
+    switch ((d + 3) / 4) {
+    case 1: k_nearest_ref<4><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    case 2: k_nearest_ref<8><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    case 3: k_nearest_ref<12><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    case 4: k_nearest_ref<16><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    case 5: k_nearest_ref<20><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    case 6: k_nearest_ref<24><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    case 7: k_nearest_ref<28><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    default: k_nearest_ref<32><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    }
     count_launches(1);
     return cudaGetLastError();
 }
@@ -688,13 +720,6 @@ __device__ __forceinline__ uint16_t round16(double v, int fp16, double *exact)
     return __bfloat16_as_ushort(h);
 }
 
-// Element offset of (row i, K index k) in the core-matrix interleaved operand layout:
-// 8-row groups, each holding kpad/8 core matrices of 8 rows x 8 elements (16 bytes).
-__device__ __forceinline__ int64_t il_offset(int64_t i, int k, int kpad)
-{
-    return (((i >> 3) * (kpad >> 3) + (k >> 3)) * 8 + (i & 7)) * 8 + (k & 7);
-}
-
 // Tensor-core operands.  With y = (x - mu) * scale (scale a power of two) and x_hat
 // its 16-bit approximation, the accumulator of the row operand A_i against the column
 // operand B_j is |x_hat_i - x_hat_j|^2 (+ a bounded term for the split form):
@@ -707,94 +732,132 @@ __device__ __forceinline__ int64_t il_offset(int64_t i, int k, int kpad)
 // (|x_hat| for one term, |hi| + |lo| for the split form); E = the norm split's residual
 // plus, for the split form, |lo|^2 (2 lo_i.lo_j <= |lo_i|^2 + |lo_j|^2).  These bound
 // the candidate error in the re-rank's completeness test.
-__global__ void k_tc_operands(const float *__restrict__ X, int64_t N, int d, const double *__restrict__ mu,
-                              double scale, int fp16, int terms, int kpad, int64_t Npad,
-                              const uint32_t *__restrict__ row2pos, uint16_t *__restrict__ XA,
-                              uint16_t *__restrict__ XB, float *__restrict__ r_out, float *__restrict__ P_out,
-                              float *__restrict__ E_out, unsigned long long *max_bits)
+constexpr int kOpThreads = 64;   // positions per block (a multiple of 8: whole core-matrix groups)
+
+// One thread per position; the row's 16-bit values are assembled in shared memory and the
+// block writes its positions' region of XA / XB with 16-byte stores.  Layout (core-matrix
+// interleaved): element (position p, K index k) sits at
+//     (((p / 8) * (kpad / 8) + k / 8) * 8 + p % 8) * 8 + k % 8,
+// 8-position groups of kpad/8 core matrices (8 rows x 16 bytes), so the positions of one
+// block (a multiple of 8) own one contiguous region.
+__global__ void __launch_bounds__(kOpThreads) k_tc_operands(const float *__restrict__ X, int64_t N, int d,
+                                                            const double *__restrict__ mu, double scale, int fp16,
+                                                            int terms, int kpad, int64_t Npad,
+                                                            const uint32_t *__restrict__ pos2row,
+                                                            uint16_t *__restrict__ XA, uint16_t *__restrict__ XB,
+                                                            float *__restrict__ r_out, float *__restrict__ P_out,
+                                                            float *__restrict__ E_out, unsigned long long *max_bits)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Npad) return;
+    extern __shared__ __align__(16) uint16_t op_sm[];   // [2][kOpThreads][kpad]
+    uint16_t *sa = op_sm + (size_t)threadIdx.x * kpad;
+    uint16_t *sb = op_sm + (size_t)(kOpThreads + threadIdx.x) * kpad;
+    const int64_t p = (int64_t)blockIdx.x * kOpThreads + threadIdx.x;   // position (< Npad)
     const uint16_t one = fp16 ? (uint16_t)0x3C00 : (uint16_t)0x3F80;
     const int D = terms * d;   // product columns
-    if (i >= N) {
+    float rf = 0.0f, Pf = 0.0f, Ef = 0.0f;
+    if (p >= N) {
         // padding column: a huge accumulator; padding row: zeros (never read back)
         const uint16_t big = fp16 ? (uint16_t)0x7800 /* 32768 */ : (uint16_t)0x7180 /* 2^100 */;
         for (int k = 0; k < kpad; ++k) {
-            XA[il_offset(i, k, kpad)] = 0;
-            XB[il_offset(i, k, kpad)] = (k >= D && k < D + 3) ? big : (uint16_t)0;
+            sa[k] = 0;
+            sb[k] = (k >= D && k < D + 3) ? big : (uint16_t)0;
         }
-        return;
-    }
-    const int64_t pos = row2pos[i];   // operands are stored in position order
-    double rr = 0.0, n = 0.0, ynorm2 = 0.0, hn = 0.0, ln = 0.0;
-    for (int k = 0; k < d; ++k) {
-        const double y = ((double)X[i * d + k] - mu[k]) * scale;
-        double h, l = 0.0, t;
-        const uint16_t hb = round16(y, fp16, &h);
-        uint16_t lb = 0;
-        if (terms == 3) lb = round16(y - h, fp16, &l);
-        const double xh = h + l;   // exact: both are 16-bit values of nearby binades
-        rr += (xh - y) * (xh - y);
-        n += xh * xh;
-        ynorm2 += y * y;
-        hn += h * h;
-        ln += l * l;
-        // -2 * v is exact in either format (sign flip, exponent + 1)
-        const uint16_t hb2 = round16(-2.0 * h, fp16, &t);
-        if (terms == 1) {
-            XA[il_offset(pos, k, kpad)] = hb;
-            XB[il_offset(pos, k, kpad)] = hb2;
-        } else {
-            const uint16_t lb2 = round16(-2.0 * l, fp16, &t);
-            XA[il_offset(pos, k, kpad)] = hb;
-            XA[il_offset(pos, d + k, kpad)] = hb;
-            XA[il_offset(pos, 2 * d + k, kpad)] = lb;
-            XB[il_offset(pos, k, kpad)] = hb2;
-            XB[il_offset(pos, d + k, kpad)] = lb2;
-            XB[il_offset(pos, 2 * d + k, kpad)] = hb2;
+    } else {
+        const int64_t i = pos2row[p];
+        double rr = 0.0, n = 0.0, ynorm2 = 0.0, hn = 0.0, ln = 0.0;
+        for (int k = 0; k < d; ++k) {
+            const double y = ((double)X[i * d + k] - mu[k]) * scale;
+            double h, l = 0.0, t;
+            const uint16_t hb = round16(y, fp16, &h);
+            uint16_t lb = 0;
+            if (terms == 3) lb = round16(y - h, fp16, &l);
+            const double xh = h + l;   // exact: both are 16-bit values of nearby binades
+            rr += (xh - y) * (xh - y);
+            n += xh * xh;
+            ynorm2 += y * y;
+            hn += h * h;
+            ln += l * l;
+            // -2 * v is exact in either format (sign flip, exponent + 1)
+            const uint16_t hb2 = round16(-2.0 * h, fp16, &t);
+            if (terms == 1) {
+                sa[k] = hb;
+                sb[k] = hb2;
+            } else {
+                const uint16_t lb2 = round16(-2.0 * l, fp16, &t);
+                sa[k] = hb;
+                sa[d + k] = hb;
+                sa[2 * d + k] = lb;
+                sb[k] = hb2;
+                sb[d + k] = lb2;
+                sb[2 * d + k] = hb2;
+            }
         }
-    }
-    double a1, a2, a3;
-    uint16_t b1 = round16(n, fp16, &a1);
-    double rem = n - a1;
-    uint16_t b2 = round16(rem, fp16, &a2);
-    double rem2 = rem - a2;
-    uint16_t b3 = round16(rem2, fp16, &a3);
-    double E = fabs(rem2 - a3) + ln;
-    for (int k = D; k < kpad; ++k) {
-        uint16_t va = 0, vb = 0;
-        if (k < D + 3) {
-            va = one;
-            vb = k == D ? b1 : (k == D + 1 ? b2 : b3);
-        } else if (k < D + 6) {
-            va = k == D + 3 ? b1 : (k == D + 4 ? b2 : b3);
-            vb = one;
+        double a1, a2, a3;
+        const uint16_t b1 = round16(n, fp16, &a1);
+        const double rem = n - a1;
+        const uint16_t b2 = round16(rem, fp16, &a2);
+        const double rem2 = rem - a2;
+        const uint16_t b3 = round16(rem2, fp16, &a3);
+        double E = fabs(rem2 - a3) + ln;
+        for (int k = D; k < kpad; ++k) {
+            uint16_t va = 0, vb = 0;
+            if (k < D + 3) {
+                va = one;
+                vb = k == D ? b1 : (k == D + 1 ? b2 : b3);
+            } else if (k < D + 6) {
+                va = k == D + 3 ? b1 : (k == D + 4 ? b2 : b3);
+                vb = one;
+            }
+            sa[k] = va;
+            sb[k] = vb;
         }
-        XA[il_offset(pos, k, kpad)] = va;
-        XB[il_offset(pos, k, kpad)] = vb;
+        // rounding radius: |x_hat - y| plus the binary64 error of (x - mu) * scale, both
+        // enlarged by a relative 1e-12 for the roundings of these bound computations
+        const double r = (sqrt(rr) + sqrt(ynorm2) * 0x1p-52) * (1.0 + 1e-12) + 1e-300;
+        const double P = (terms == 1 ? sqrt(n) : sqrt(hn) + sqrt(ln)) * (1.0 + 1e-12);
+        E = E * (1.0 + 1e-12);
+        rf = __double2float_ru(r);
+        Pf = __double2float_ru(P);
+        Ef = __double2float_ru(E);
+        r_out[i] = rf;
+        P_out[i] = Pf;
+        E_out[i] = Ef;
     }
-    // rounding radius: |x_hat - y| plus the binary64 error of (x - mu) * scale, both
-    // enlarged by a relative 1e-12 for the roundings of these bound computations
-    double r = (sqrt(rr) + sqrt(ynorm2) * 0x1p-52) * (1.0 + 1e-12) + 1e-300;
-    double P = (terms == 1 ? sqrt(n) : sqrt(hn) + sqrt(ln)) * (1.0 + 1e-12);
-    E = E * (1.0 + 1e-12);
-    float rf = __double2float_ru(r), Pf = __double2float_ru(P), Ef = __double2float_ru(E);
-    r_out[i] = rf;
-    P_out[i] = Pf;
-    E_out[i] = Ef;
-    atomic_max_nonneg(&max_bits[0], (double)rf);
-    atomic_max_nonneg(&max_bits[1], (double)Pf);
-    atomic_max_nonneg(&max_bits[2], (double)Ef);
+    // maxima: one atomic per warp (non-negative floats order as their bits)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        rf = fmaxf(rf, __shfl_xor_sync(0xffffffffu, rf, o));
+        Pf = fmaxf(Pf, __shfl_xor_sync(0xffffffffu, Pf, o));
+        Ef = fmaxf(Ef, __shfl_xor_sync(0xffffffffu, Ef, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&max_bits[0], (double)rf);
+        atomic_max_nonneg(&max_bits[1], (double)Pf);
+        atomic_max_nonneg(&max_bits[2], (double)Ef);
+    }
+    __syncthreads();
+    // copy-out: uint4 u of the block's region is row (u / (8 cpr)) * 8 + u % 8 of the
+    // block, chunk (u / 8) % cpr
+    const int cpr = kpad >> 3;
+    const int nu = kOpThreads * cpr;
+    uint4 *ga = reinterpret_cast<uint4 *>(XA) + (int64_t)blockIdx.x * nu;
+    uint4 *gb = reinterpret_cast<uint4 *>(XB) + (int64_t)blockIdx.x * nu;
+    for (int u = threadIdx.x; u < nu; u += kOpThreads) {
+        const int gl = u / (cpr * 8), rem = u - gl * cpr * 8, c = rem >> 3, row = gl * 8 + (rem & 7);
+        ga[u] = *reinterpret_cast<const uint4 *>(op_sm + (size_t)row * kpad + c * 8);
+        gb[u] = *reinterpret_cast<const uint4 *>(op_sm + (size_t)(kOpThreads + row) * kpad + c * 8);
+    }
 }
 
 cudaError_t launch_tc_operands(const float *X, int64_t N, int d, const double *mu, double scale, int fp16, int terms,
-                               int kpad, int64_t Npad, const uint32_t *row2pos, uint16_t *XA, uint16_t *XB, float *r,
+                               int kpad, int64_t Npad, const uint32_t *pos2row, uint16_t *XA, uint16_t *XB, float *r,
                                float *P, float *E, unsigned long long *max_bits, cudaStream_t s)
 {
-    int blocks = (int)((Npad + 255) / 256);
-    k_tc_operands<<<blocks, 256, 0, s>>>(X, N, d, mu, scale, fp16, terms, kpad, Npad, row2pos, XA, XB, r, P, E,
-                                         max_bits);
+    if (Npad % kOpThreads != 0 || kpad % 16 != 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)2 * kOpThreads * kpad * sizeof(uint16_t);   // <= 28 KB (kpad <= 112)
+    const unsigned blocks = (unsigned)(Npad / kOpThreads);
+    k_tc_operands<<<blocks, kOpThreads, smem, s>>>(X, N, d, mu, scale, fp16, terms, kpad, Npad, pos2row, XA, XB, r, P,
+                                                   E, max_bits);
     count_launches(1);
     return cudaGetLastError();
 }
