@@ -250,6 +250,8 @@ SelConst make_selconst(const Margin &m)
     sc.R = up_f(m.R * grow);
     sc.Pmax = up_f(m.Pmax * grow);
     sc.Emax = up_f(m.Emax * grow);
+    sc.c1_32 = up_f((1.0 + m.gamma32) / (1.0 - m.gamma32) * grow * grow);
+    sc.c0_32 = up_f(m.alpha32 * grow + 1e-37);
     return sc;
 }
 
@@ -426,6 +428,7 @@ nnm_status collect(nnm_ctx *c, const uint32_t *rows, const float *thr, int64_t n
             ra.scratch_D = c->coll_D;
             ra.k = k;
             ra.m = c->margin;
+            ra.sc = c->selc;
             ra.res_j = res_j;
             ra.res_D = res_D;
             ra.res_n = res_n;
@@ -526,6 +529,7 @@ nnm_status run_knn(nnm_ctx *c, const uint32_t *rows, int64_t nslots, int k, cons
         fa.in_ovf = c->cand_ovf;
         fa.k = k;
         fa.m = c->margin;
+        fa.sc = c->selc;
         fa.res_j = res_j;
         fa.res_D = res_D;
         fa.res_n = res_n;

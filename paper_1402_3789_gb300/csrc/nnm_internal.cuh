@@ -67,6 +67,7 @@ struct SelConst {
     float c1, c0;   // FP32 path: T = (v + c0) * c1 + c0
     float gamma;    // tensor path: accumulation bound
     float R, Pmax, Emax;
+    float c1_32, c0_32;   // the re-rank's FP32 refinement: T32 = (v + c0_32) * c1_32 + c0_32
 };
 
 // ---------------------------------------------------------------------------------
@@ -222,6 +223,7 @@ struct FinalizeArgs {
     const uint8_t *in_ovf;     // [nslots][splits]
     int k;                     // results per row
     Margin m;
+    SelConst sc;               // FP32 upper bounds of the thresholds (as the sweeps use them)
     // results (indexed by row)
     uint32_t *res_j;           // [N][k]
     double *res_D;             // [N][k]
@@ -254,7 +256,8 @@ struct CollectRerankArgs {
     int64_t cap;
     double *scratch_D;         // [n][cap]
     int k;
-    Margin m;                  // FP32 refinement bounds
+    Margin m;
+    SelConst sc;               // FP32 refinement bounds
     uint32_t *res_j;
     double *res_D;
     uint8_t *res_n;

@@ -8,11 +8,14 @@
 // every operation IEEE binary64 round-to-nearest without contraction, and the k
 // smallest (D, j) are kept.  Completeness: a candidate value v approximates the exact
 // squared distance within a proven bound; from the k-th smallest v the re-rank derives a
-// threshold T such that every column of the exact top k has v <= T.  Each column range
+// threshold T such that every column of the exact top k has v <= T (in FP32 rounded
+// upwards: the sweeps' own bound of select.cuh, which dominates the binary64 bound of
+// the error analysis; a larger T only keeps more).  Each column range
 // of the sweep kept every eligible value <= its own running bound, which is >= T,
 // unless its band overflowed; a row with an overflowed range goes to the collect pass
 // (every eligible column with v <= T) instead.
 #include "nnm_internal.cuh"
+#include "select.cuh"
 
 namespace nnm {
 
@@ -23,25 +26,6 @@ constexpr int kFinWarps = 4;
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v)
 {
     if (p) atomicMax(p, (unsigned long long)__double_as_longlong(v));
-}
-
-// Threshold T from the k-th smallest candidate value vk (see the file comment).
-__device__ double threshold(const Margin &m, uint32_t i, float vk)
-{
-    if (!(vk < INFINITY)) return INFINITY;
-    const double grow = 1.0 + 1e-12;
-    if (!m.tensor) {
-        // FP32 direct: |v - s| <= gamma*s + alpha, s the exact squared distance
-        const double us = ((double)vk + m.alpha) / (1.0 - m.gamma) * grow;
-        return (us * (1.0 + m.gamma) + m.alpha) * grow;
-    }
-    // tensor core (scaled units): |v - |x_hat_i - x_hat_j|^2| <= eps_i and
-    // | |x_hat_i - x_hat_j| - scale*sqrt(s) | <= r_i + r_j
-    const double Pi = (double)m.P[i];
-    const double eps = m.gamma * (Pi + m.Pmax) * (Pi + m.Pmax) + (double)m.E[i] + m.Emax;
-    const double rr = (double)m.r[i] + m.R;
-    const double U = (sqrt((double)vk + eps) + rr) * grow;
-    return ((U + rr) * (U + rr) + eps) * grow;
 }
 
 // Selections compare keys as integers: the bits of a non-negative double (or float)
@@ -147,45 +131,71 @@ __device__ __forceinline__ float fp32_D(const float *__restrict__ xi, const floa
     return s;
 }
 
+// Per-warp shared scratch of exact_distances: the products of up to 32 candidates
+// (row stride d rounded up to odd: no bank conflicts) and their column / entry indices.
+__host__ __device__ inline int ed_stride(int d) { return d | 1; }
+__host__ __device__ inline size_t ed_scratch_bytes(int d) { return (size_t)32 * ed_stride(d) * 8 + 64 * 4; }
+
 // Exact distances of the candidates in wD (entries 0, others +inf) of one row, cheapest
 // first: with refine, every candidate first gets its FP32 direct value s; from the k-th
-// smallest s the FP32 bound T32 (as for the FP32 sweep) keeps only the candidates that
-// can still be among the exact k nearest, and only those get the binary64 distance.
-// On return wD[e] = D (binary64) or +inf.  Returns the number of binary64 evaluations.
+// smallest s the FP32 bound T32 (as for the FP32 sweep, rounded up) keeps only the
+// candidates that can still be among the exact k nearest, and only those get the
+// binary64 distance.  The binary64 work is canon_D's, operation for operation and in the
+// same order, with the lanes kept busy: for the marked entries of each run of 32, the
+// products (or absolute differences) of all (candidate, feature) pairs are spread over
+// the lanes, then one lane per candidate sums (or takes the max of) them in feature
+// order.  On return wD[e] = D (binary64) or +inf.  Returns the number of binary64
+// evaluations.
 __device__ int exact_distances(const float *xi, const float *X, int d, double *wD, const uint32_t *wj, int n, int k,
-                               const Margin &m, bool refine)
+                               const SelConst &sc, int metric, bool refine, uint8_t *scratch)
 {
     const int lane = threadIdx.x & 31;
     long long *kk = reinterpret_cast<long long *>(wD);
-    long long lim = kInfD;   // entries with key <= lim (and not +inf) get the exact distance
     if (refine) {
         // float keys of s in place of the marks (+inf keys for non-candidates)
         for (int e = lane; e < n; e += 32)
-            kk[e] = kk[e] < kInfD ? (long long)__float_as_int(fp32_D(xi, X + (int64_t)wj[e] * d, d, m.metric)) : kNone;
+            kk[e] = kk[e] < kInfD ? (long long)__float_as_int(fp32_D(xi, X + (int64_t)wj[e] * d, d, metric)) : kNone;
         __syncwarp();
         int taken = 0;
         const float vk = kth_float(kk, n, k, &taken);
-        float t32 = INFINITY;
-        if (taken == k) {
-            const double grow = 1.0 + 1e-12;
-            const double us = ((double)vk + m.alpha32) / (1.0 - m.gamma32) * grow;
-            t32 = __double2float_ru((us * (1.0 + m.gamma32) + m.alpha32) * grow);
-        }
-        lim = (long long)__float_as_int(t32);   // +inf: every candidate
+        const float t32 = taken == k ? __fadd_ru(__fmul_ru(__fadd_ru(vk, sc.c0_32), sc.c1_32), sc.c0_32) : INFINITY;
+        const long long lim = (long long)__float_as_int(t32);   // +inf: every candidate
         for (int e = lane; e < n; e += 32) kk[e] = kk[e] <= lim ? 0LL : kInfD;   // back to marks
         __syncwarp();
     }
+    const int stride = ed_stride(d);
+    double *tsm = reinterpret_cast<double *>(scratch);
+    uint32_t *cj = reinterpret_cast<uint32_t *>(scratch + (size_t)32 * stride * 8);   // [32] columns, [32] entries
     int nd = 0;
-    for (int e = lane; e < n; e += 32) {
-        double D = INFINITY;
-        if (kk[e] == 0LL) {
-            D = canon_D(xi, X + (int64_t)wj[e] * d, d, m.metric);
-            ++nd;
+    for (int base = 0; base < n; base += 32) {
+        const int e = base + lane;
+        const bool mk = e < n && kk[e] == 0LL;
+        const unsigned int bm = __ballot_sync(0xffffffffu, mk);
+        const int nb = __popc(bm);
+        if (mk) {
+            const int slot = __popc(bm & ((1u << lane) - 1u));
+            cj[slot] = wj[e];
+            cj[32 + slot] = (uint32_t)e;
+        } else if (e < n) {
+            wD[e] = INFINITY;
         }
-        wD[e] = D;
+        __syncwarp();
+        for (int q = lane; q < nb * d; q += 32) {
+            const int c = q / d, f = q - c * d;
+            const double ev = __dsub_rn((double)xi[f], (double)X[(int64_t)cj[c] * d + f]);
+            tsm[c * stride + f] = metric == 0 ? __dmul_rn(ev, ev) : fabs(ev);
+        }
+        __syncwarp();
+        if (lane < nb) {
+            const double *t = tsm + lane * stride;
+            double D = t[0];
+            for (int f = 1; f < d; ++f) D = metric == 2 ? fmax(D, t[f]) : __dadd_rn(D, t[f]);
+            wD[cj[32 + lane]] = D;
+        }
+        nd += nb;
+        __syncwarp();
     }
-    __syncwarp();
-    return __reduce_add_sync(0xffffffffu, nd);
+    return nd;
 }
 
 __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs a)
@@ -196,10 +206,10 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     double *wD = reinterpret_cast<double *>(smem) + (size_t)warp * n_ent;
     float *wv = reinterpret_cast<float *>(reinterpret_cast<double *>(smem) + (size_t)kFinWarps * n_ent) +
                 (size_t)warp * n_ent;
-    uint32_t *wj = reinterpret_cast<uint32_t *>(reinterpret_cast<float *>(reinterpret_cast<double *>(smem) +
-                                                                          (size_t)kFinWarps * n_ent) +
-                                                (size_t)kFinWarps * n_ent) +
-                   (size_t)warp * n_ent;
+    uint32_t *wj_all = reinterpret_cast<uint32_t *>(reinterpret_cast<float *>(reinterpret_cast<double *>(smem) +
+                                                                              (size_t)kFinWarps * n_ent) +
+                                                    (size_t)kFinWarps * n_ent);
+    uint32_t *wj = wj_all + (size_t)warp * n_ent;
     const int64_t q = (int64_t)blockIdx.x * kFinWarps + warp;
     if (q >= a.nslots) return;
     const uint32_t ipos = a.rows ? a.rows[q] : (uint32_t)q;
@@ -224,19 +234,21 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_finalize(const FinalizeArgs 
     // a bounded row needs only columns with D <= B: their candidate values are at most
     // the threshold of the value B (in candidate units)
     const double B = a.row_B ? a.row_B[i] : INFINITY;
-    double T = threshold(a.m, i, taken < a.k ? INFINITY : vk);
-    if (B < INFINITY) T = fmin(T, threshold(a.m, i, __double2float_ru(B / a.m.inv_scale2)));
+    const RowConst rc = make_rowconst(a.sc, a.m, i);
+    float T = sel_threshold(a.sc, rc, taken < a.k ? INFINITY : vk);
+    if (B < INFINITY) T = fminf(T, sel_threshold(a.sc, rc, __double2float_ru(B / a.m.inv_scale2)));
     const bool any_ovf = __any_sync(0xffffffffu, ovf);
     if (lane == 0) {
         a.ovf_flag[q] = any_ovf ? 1 : 0;
-        if (any_ovf) a.ovf_thr[q] = __double2float_ru(T);
+        if (any_ovf) a.ovf_thr[q] = T;
     }
     if (any_ovf) return;
     const float *xi = a.X + (int64_t)i * a.d;
-    const float Tf = __double2float_ru(T);   // >= T: keeps a superset
+    const float Tf = T;
     for (int e = lane; e < n_ent; e += 32) wD[e] = (wj[e] != kInvalid && wv[e] <= Tf) ? 0.0 : INFINITY;
     __syncwarp();
-    const int nc = exact_distances(xi, a.X, a.d, wD, wj, n_ent, a.k, a.m, a.m.tensor != 0);
+    uint8_t *scratch = reinterpret_cast<uint8_t *>(wj_all + (size_t)kFinWarps * n_ent) + (size_t)warp * ed_scratch_bytes(a.d);
+    const int nc = exact_distances(xi, a.X, a.d, wD, wj, n_ent, a.k, a.sc, a.m.metric, a.m.tensor != 0, scratch);
     if (B < INFINITY) {
         const long long kb = dkey(B);
         for (int e = lane; e < n_ent; e += 32)
@@ -299,7 +311,9 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
     }
     __syncwarp();
     __threadfence_block();
-    const int nd = exact_distances(xi, a.X, a.d, wD, wj, (int)cnt, a.k, a.m, true);
+    extern __shared__ __align__(16) uint8_t cr_smem[];
+    uint8_t *scratch = cr_smem + (size_t)warp * ed_scratch_bytes(a.d);
+    const int nd = exact_distances(xi, a.X, a.d, wD, wj, (int)cnt, a.k, a.sc, a.m.metric, true, scratch);
     const double B = a.row_B ? a.row_B[i] : INFINITY;
     if (B < INFINITY)
         for (uint32_t e = lane; e < cnt; e += 32)
@@ -320,7 +334,8 @@ __global__ void __launch_bounds__(kFinWarps * 32) k_collect_rerank(const Collect
 cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s)
 {
     if (a.nslots <= 0) return cudaSuccess;
-    const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4);   // <= 160 KB
+    const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4) +   // <= 160 KB
+                        (size_t)kFinWarps * ed_scratch_bytes(a.d);             // <= 35 KB
     cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((a.nslots + kFinWarps - 1) / kFinWarps);
@@ -333,7 +348,7 @@ cudaError_t launch_collect_rerank(const CollectRerankArgs &a, cudaStream_t s)
 {
     if (a.n <= 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((a.n + kFinWarps - 1) / kFinWarps);
-    k_collect_rerank<<<blocks, kFinWarps * 32, 0, s>>>(a);
+    k_collect_rerank<<<blocks, kFinWarps * 32, (size_t)kFinWarps * ed_scratch_bytes(a.d), s>>>(a);
     count_launches(1);
     return cudaGetLastError();
 }
