@@ -43,7 +43,7 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="override N (smaller runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--compare", default="fp16,bf16,fp32", help="comma list of other precisions timed for one step each")
+    p.add_argument("--compare", default="fp16,bf16,fp32", help="comma list of other precisions timed for one step each (after one untimed step)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--ref-seconds", type=float, default=None, help="oracle seconds per step of --impl reference")
     return p.parse_args()
@@ -334,9 +334,11 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "clocks": clocks,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
 
-    # the other precisions named by --compare, one step each
+    # the other precisions named by --compare, one timed step each after one untimed step
+    # (the first use of a precision's kernels pays their lazy module loading)
     comp = {}
     for p in [c for c in args.compare.split(",") if c and c != args.precision]:
+        step(p)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
