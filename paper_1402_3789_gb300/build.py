@@ -19,13 +19,11 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 # translation units: (output name, source, extra defines)
-UNITS = [
+# (the FP32 sweep once per feature width, and the long units first)
+UNITS = [(f"sweep_fp32_d{D}", "sweep_fp32.cu", [f"-DNNM_SWEEP_FP32_D={D}"]) for D in (25, 32, 28, 24, 20, 16, 12, 8, 4)] + [
+    ("sweep_tc", "sweep_tc.cu", []),
     ("nnm_api", "nnm_api.cu", []),
     ("prep", "prep.cu", []),
-    ("sweep_fp32_a", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_A"]),
-    ("sweep_fp32_b", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_B"]),
-    ("sweep_fp32_c", "sweep_fp32.cu", ["-DNNM_SWEEP_FP32_C"]),
-    ("sweep_tc", "sweep_tc.cu", []),
     ("rerank", "rerank.cu", []),
     ("rounds", "rounds.cu", []),
     ("sort", "sort.cu", []),

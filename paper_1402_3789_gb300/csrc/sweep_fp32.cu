@@ -404,43 +404,43 @@ cudaError_t launch_d(const SweepArgs &a, bool collect, cudaStream_t s)
 
 }  // namespace
 
-// one group of instantiations per translation unit (this file is compiled three times)
-cudaError_t launch_sweep_fp32_a(const SweepArgs &a, int d, bool collect, cudaStream_t s);
-cudaError_t launch_sweep_fp32_b(const SweepArgs &a, int d, bool collect, cudaStream_t s);
-cudaError_t launch_sweep_fp32_c(const SweepArgs &a, int d, bool collect, cudaStream_t s);
+// One width D per translation unit (this file is compiled once per D, with
+// -DNNM_SWEEP_FP32_D=D, so that the instantiations compile in parallel); the dispatcher
+// lives in the D = 32 unit.
+cudaError_t launch_sweep_fp32_d4(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d8(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d12(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d16(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d20(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d24(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d25(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d28(const SweepArgs &a, bool collect, cudaStream_t s);
+cudaError_t launch_sweep_fp32_d32(const SweepArgs &a, bool collect, cudaStream_t s);
 
-#ifdef NNM_SWEEP_FP32_A
-cudaError_t launch_sweep_fp32_a(const SweepArgs &a, int d, bool collect, cudaStream_t s)
+#ifdef NNM_SWEEP_FP32_D
+#define NNM_FP32_UNIT_NAME2(x) launch_sweep_fp32_d##x
+#define NNM_FP32_UNIT_NAME(x) NNM_FP32_UNIT_NAME2(x)
+cudaError_t NNM_FP32_UNIT_NAME(NNM_SWEEP_FP32_D)(const SweepArgs &a, bool collect, cudaStream_t s)
 {
-    if (d <= 4) return launch_d<4>(a, collect, s);
-    if (d <= 8) return launch_d<8>(a, collect, s);
-    return launch_d<12>(a, collect, s);
+    return launch_d<NNM_SWEEP_FP32_D>(a, collect, s);
 }
-#endif
+#undef NNM_FP32_UNIT_NAME
+#undef NNM_FP32_UNIT_NAME2
 
-#ifdef NNM_SWEEP_FP32_B
-cudaError_t launch_sweep_fp32_b(const SweepArgs &a, int d, bool collect, cudaStream_t s)
-{
-    if (d <= 16) return launch_d<16>(a, collect, s);
-    if (d <= 20) return launch_d<20>(a, collect, s);
-    return launch_d<24>(a, collect, s);
-}
-#endif
-
-#ifdef NNM_SWEEP_FP32_C
-cudaError_t launch_sweep_fp32_c(const SweepArgs &a, int d, bool collect, cudaStream_t s)
-{
-    if (d == 25) return launch_d<25>(a, collect, s);
-    if (d <= 28) return launch_d<28>(a, collect, s);
-    return launch_d<32>(a, collect, s);
-}
-
+#if NNM_SWEEP_FP32_D == 32
 cudaError_t launch_sweep_fp32(const SweepArgs &a, int d, bool collect, cudaStream_t s)
 {
-    if (d <= 12) return launch_sweep_fp32_a(a, d, collect, s);
-    if (d <= 24) return launch_sweep_fp32_b(a, d, collect, s);
-    return launch_sweep_fp32_c(a, d, collect, s);
+    if (d <= 4) return launch_sweep_fp32_d4(a, collect, s);
+    if (d <= 8) return launch_sweep_fp32_d8(a, collect, s);
+    if (d <= 12) return launch_sweep_fp32_d12(a, collect, s);
+    if (d <= 16) return launch_sweep_fp32_d16(a, collect, s);
+    if (d <= 20) return launch_sweep_fp32_d20(a, collect, s);
+    if (d <= 24) return launch_sweep_fp32_d24(a, collect, s);
+    if (d == 25) return launch_sweep_fp32_d25(a, collect, s);
+    if (d <= 28) return launch_sweep_fp32_d28(a, collect, s);
+    return launch_sweep_fp32_d32(a, collect, s);
 }
+#endif
 #endif
 
 }  // namespace nnm
