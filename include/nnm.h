@@ -82,12 +82,14 @@ typedef struct {
                               (the restricted result is unchanged; the merge tree returned
                               by nnm_get_tree then holds only edges within the cap)        */
     int32_t col_split;     /* 0: automatic; >0: number of column ranges per row tile      */
-    int32_t no_tile_pruning; /* 1: evaluate every column tile (no bounding-sphere skipping;
-                                results are identical, only slower)                        */
+    int32_t no_tile_pruning; /* 1: evaluate every column tile (no skipping by bounding
+                                spheres or landmark distances; results are identical,
+                                only slower)                                               */
 } nnm_options;
 
 /* Restrictions ("Problem statement"; "Problem settings").  Zero disables each one.
- *   max_join_dist      > 0 and finite: a pair joins only if D <= fl64(c*c).
+ *   max_join_dist      > 0 and finite: a pair joins only if D <= fl64(c*c) (Euclidean;
+ *                      D <= c for the other metrics).
  *   kl1_stop_clusters  KL1: no join once the number of clusters has reached KL1.
  *   kl2_max_pre_size   KL2: no join if either cluster already has more than KL2 rows
  *                      (a cluster may end larger than KL2, as the paper allows).
