@@ -86,3 +86,13 @@ def test_batched_create_rejects_bad_offsets_without_touching_the_gpu(lib):
         arr = (ctypes.c_int64 * len(offs))(*offs)
         st = lib.nnm_create_batched(P(16), ctypes.cast(arr, P), len(offs) - 1, 4, 0, 0, None, None, ctypes.byref(out))
         assert st == 1 and not out.value, offs   # NNM_EINVAL
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the CUDA library absent the binding raises instead of
+    computing anything."""
+    from paper_1402_3789_gb300 import nnm
+    monkeypatch.setattr(nnm, "_LIB", None)
+    monkeypatch.setattr(nnm, "library_path", lambda: str(tmp_path / "libnnm.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        nnm.load_library()
