@@ -57,7 +57,9 @@ def test_full_size_sampled_rows_tree_and_restrictions(nnm, orc, workload, precis
     N = X.shape[0]
     Xd = dev(X)
     rng = np.random.default_rng(123)
-    rows = np.sort(rng.choice(N, size=600, replace=False))
+    # 10,000 sampled rows at the paper-scale sizes (the oracle's brute force on the host
+    # cores takes about 20 s at N = 2M), 2,000 at the smaller one
+    rows = np.sort(rng.choice(N, size=10_000 if N >= 1_000_000 else 2_000, replace=False))
     oi, oD = orc.knn(X, 8, queries=rows)
     trees = []
     for p in precisions:
