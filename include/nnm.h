@@ -246,9 +246,16 @@ void nnm_destroy(nnm_ctx *ctx);
  * pool; services with a memory budget fixed at start-up).  Its scratch is one fixed
  * device array of about 21 MB inside this library, held on every GPU that loads the
  * library until the process exits.
- *   tree_dev       nnm_edge [n_edges] device, sorted by key (as nnm_get_tree returns it);
- *                  0 <= n_edges <= N-1.
+ *   tree_dev       nnm_edge [n_edges] device, one instance's tree sorted by key, as
+ *                  nnm_get_tree returns it for a context of one instance (a batched
+ *                  context's tree, grouped by instance, is not accepted);
+ *                  0 <= n_edges <= N-1.  Checked on the device before the walk: every
+ *                  endpoint below N, a < b, D finite and >= 0, keys strictly increasing;
+ *                  a tree that fails gives NNM_EINVAL and no result.
  *   N              rows, 2 <= N <= NNM_STATIC_MAX_ROWS (larger N: NNM_EUNSUPPORTED, no launch).
+ *   metric         the metric the tree's D values are in (the context's metric): it fixes
+ *                  the cap's units and the merges' reported length, as for nnm_cluster;
+ *                  an unknown value gives NNM_EINVAL.
  *   restrictions   as for nnm_cluster (may be NULL); same EINVAL / EUNSUPPORTED rules.
  *   merges_dev, n_merges_host, labels_dev, n_clusters_host  as for nnm_cluster.
  *   cuda_stream    cudaStream_t to enqueue on (NULL: the legacy default stream); the call
@@ -257,7 +264,7 @@ void nnm_destroy(nnm_ctx *ctx);
  * device current; make it before any stream capture.  All calls share the array: calls
  * whose work overlaps on the GPU race and corrupt each other; calls ordered on one
  * stream are safe.  Errors: EINVAL, EUNSUPPORTED, ECUDA. */
-nnm_status nnm_restrict_static(const nnm_edge *tree_dev, int64_t n_edges, int64_t N,
+nnm_status nnm_restrict_static(const nnm_edge *tree_dev, int64_t n_edges, int64_t N, nnm_metric metric,
                                const nnm_restrictions *restrictions, nnm_merge *merges_dev,
                                int64_t *n_merges_host, int32_t *labels_dev, int64_t *n_clusters_host,
                                void *cuda_stream);

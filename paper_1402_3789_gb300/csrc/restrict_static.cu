@@ -16,7 +16,9 @@
 //     different host threads without ordering) race and corrupt each other's results;
 //     calls ordered on one stream are safe, each starts from its own initialisation;
 //   - the first call on a device looks up the array's device address (once per device,
-//     with that device current); make that first call before any stream capture.
+//     with that device current); make that first call before any stream capture;
+//   - the caller's tree is checked on the device (endpoints below N, key order) before
+//     the walk indexes the union-find with its endpoints; a bad tree gives NNM_EINVAL.
 #include <mutex>
 
 #include "nnm_internal.cuh"
@@ -28,12 +30,37 @@ namespace {
 constexpr int64_t kStaticMaxRows = NNM_STATIC_MAX_ROWS;
 constexpr int64_t kStaticBlocks = (kStaticMaxRows + 255) / 256;
 // layout (uint32 words): uf_parent, uf_size, deferred, minm, flag [kStaticMaxRows each],
-// block_sums [kStaticBlocks], then two 64-bit counters (n_merges, K)
-constexpr int64_t kWords = 5 * kStaticMaxRows + kStaticBlocks + 4;
+// block_sums [kStaticBlocks], then two 64-bit counters (n_merges, K) and the tree-check
+// word (bit 0: an endpoint >= N, bit 1: a == b or a > b, bit 2: D not finite and >= 0,
+// bit 3: keys not strictly increasing), padded to 8 bytes
+constexpr int64_t kCounterWord = 5 * kStaticMaxRows + kStaticBlocks;
+constexpr int64_t kWords = kCounterWord + 6;
 constexpr size_t kStaticBytes = (size_t)kWords * 4;
+static_assert(kCounterWord % 2 == 0, "64-bit counters stay aligned");
 static_assert(kStaticBytes < (size_t)24 << 20, "the fixed scratch array stays modest (~21 MB)");
 
 static __device__ __align__(256) uint32_t g_static_scratch[kWords];
+
+// The caller's tree is checked before the walk reads the union-find at its endpoints:
+// every endpoint below N, a < b, D finite and non-negative, and keys (D, a, b) strictly
+// increasing along the array (a tree grouped by instance, as a batched context returns
+// it, is not in key order across groups and fails here).  Violations set bits of *err.
+__global__ void k_check_tree(const nnm_edge *__restrict__ e, int64_t m, int64_t N, uint32_t *err)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const nnm_edge x = e[q];
+    uint32_t bits = 0;
+    if ((int64_t)x.a >= N || (int64_t)x.b >= N) bits |= 1u;
+    if (x.a >= x.b) bits |= 2u;
+    if (!(x.D >= 0.0 && x.D < INFINITY)) bits |= 4u;
+    if (q + 1 < m) {
+        const nnm_edge y = e[q + 1];
+        const bool inc = x.D < y.D || (x.D == y.D && (x.a < y.a || (x.a == y.a && x.b < y.b)));
+        if (!inc) bits |= 8u;
+    }
+    if (bits) atomicOr(err, bits);
+}
 
 // Device address of g_static_scratch per device (host code may not use the symbol's
 // host-side stand-in as a pointer).
@@ -65,12 +92,13 @@ cudaError_t scratch_address(uint32_t **out)
 using namespace nnm;
 
 extern "C" nnm_status nnm_restrict_static(const nnm_edge *tree_dev, int64_t n_edges, int64_t N,
-                                          const nnm_restrictions *restrictions, nnm_merge *merges_dev,
-                                          int64_t *n_merges_host, int32_t *labels_dev, int64_t *n_clusters_host,
-                                          void *cuda_stream)
+                                          nnm_metric metric, const nnm_restrictions *restrictions,
+                                          nnm_merge *merges_dev, int64_t *n_merges_host, int32_t *labels_dev,
+                                          int64_t *n_clusters_host, void *cuda_stream)
 {
     if (!tree_dev || !merges_dev || !n_merges_host || !labels_dev || !n_clusters_host) return NNM_EINVAL;
     if (N < 2 || n_edges < 0 || n_edges > N - 1) return NNM_EINVAL;
+    if (metric != NNM_EUCLIDEAN && metric != NNM_MANHATTAN && metric != NNM_CHEBYSHEV) return NNM_EINVAL;
     if (N > kStaticMaxRows) return NNM_EUNSUPPORTED;   // beyond the fixed scratch array
     nnm_restrictions r{};
     if (restrictions) r = *restrictions;
@@ -84,15 +112,29 @@ extern "C" nnm_status nnm_restrict_static(const nnm_edge *tree_dev, int64_t n_ed
     uint32_t *base = nullptr;
     if (scratch_address(&base) != cudaSuccess) return NNM_ECUDA;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + 5 * kStaticMaxRows + kStaticBlocks);
-    // the counters are the only state read before being written; clear them
-    if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return NNM_ECUDA;
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(base + kCounterWord);
+    uint32_t *check = base + kCounterWord + 4;
+    // the counters and the check word are the only state read before being written
+    if (cudaMemsetAsync(counters, 0, 6 * sizeof(uint32_t), s) != cudaSuccess) return NNM_ECUDA;
+    if (n_edges > 0) {
+        k_check_tree<<<(unsigned)((n_edges + 255) / 256), 256, 0, s>>>(tree_dev, n_edges, N, check);
+        count_launches(1);
+        if (cudaGetLastError() != cudaSuccess) return NNM_ECUDA;
+        uint32_t bad = 0;
+        if (cudaMemcpyAsync(&bad, check, sizeof bad, cudaMemcpyDeviceToHost, s) != cudaSuccess) return NNM_ECUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return NNM_ECUDA;
+        if (bad) return NNM_EINVAL;   // nothing was walked; the array holds no result
+    }
 
     RestrictArgs ra{};
     ra.edges = tree_dev;
     ra.m = n_edges;
     ra.N = N;
-    ra.cap2 = (r.max_join_dist > 0.0 && isfinite(r.max_join_dist)) ? r.max_join_dist * r.max_join_dist : INFINITY;
+    // the cap in D units, as nnm_cluster: squared for the squared Euclidean D
+    ra.cap2 = (r.max_join_dist > 0.0 && isfinite(r.max_join_dist))
+                  ? (metric == NNM_EUCLIDEAN ? r.max_join_dist * r.max_join_dist : r.max_join_dist)
+                  : INFINITY;
+    ra.metric = (int)metric;
     ra.kl1 = r.kl1_stop_clusters;
     ra.kl2 = r.kl2_max_pre_size;
     ra.kl3 = r.kl3_max_size;

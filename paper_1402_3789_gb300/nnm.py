@@ -105,8 +105,8 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.nnm_status_string.restype = ctypes.c_char_p
     lib.nnm_destroy.argtypes = [P]
     lib.nnm_destroy.restype = None
-    lib.nnm_restrict_static.argtypes = [P, i64, i64, ctypes.POINTER(nnm_restrictions), P, ctypes.POINTER(i64), P,
-                                        ctypes.POINTER(i64), P]
+    lib.nnm_restrict_static.argtypes = [P, i64, i64, ctypes.c_int, ctypes.POINTER(nnm_restrictions), P,
+                                        ctypes.POINTER(i64), P, ctypes.POINTER(i64), P]
     lib.nnm_restrict_static.restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -252,17 +252,18 @@ def nnm_destroy(ctx: Context) -> None:
 
 
 def nnm_restrict_static(tree_dev: torch.Tensor, n_edges: int, N: int, restrictions=None,
-                        stream: torch.cuda.Stream | None = None) -> ClusterResult:
+                        stream: torch.cuda.Stream | None = None, metric: str = "euclidean") -> ClusterResult:
     """nnm_restrict_static: restrictions + labels on a key-sorted tree (uint8 device bytes
-    of nnm_edge records), using the library's fixed scratch array (no allocation inside
-    the library; the output tensors are allocated here by the caller's allocator)."""
+    of nnm_edge records, D in the given metric), using the library's fixed scratch array
+    (no allocation inside the library; the output tensors are allocated here by the
+    caller's allocator)."""
     lib = load_library()
     stream = stream or torch.cuda.current_stream(tree_dev.device)
     merges = torch.empty(max(N - 1, 1) * MERGE_DTYPE.itemsize, dtype=torch.uint8, device=tree_dev.device)
     labels = torch.empty(N, dtype=torch.int32, device=tree_dev.device)
     r = _restrictions(restrictions)
     n_m, n_c = ctypes.c_int64(), ctypes.c_int64()
-    st = lib.nnm_restrict_static(ctypes.c_void_p(tree_dev.data_ptr()), n_edges, N, ctypes.byref(r),
+    st = lib.nnm_restrict_static(ctypes.c_void_p(tree_dev.data_ptr()), n_edges, N, METRICS[metric], ctypes.byref(r),
                                  ctypes.c_void_p(merges.data_ptr()), ctypes.byref(n_m),
                                  ctypes.c_void_p(labels.data_ptr()), ctypes.byref(n_c),
                                  ctypes.c_void_p(stream.cuda_stream))
