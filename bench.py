@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="override N (smaller runs)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-peaks", action="store_true", help="skip the FP32/FP64 peak microbenchmarks")
     p.add_argument("--compare", default="fp16,bf16,fp32", help="comma list of other precisions timed for one step each (after one untimed step)")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--ref-seconds", type=float, default=None, help="oracle seconds per step of --impl reference")
@@ -205,6 +206,40 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def measure_arith_peaks():
+    """FP32 and FP64 FMA throughput of this GPU (TFLOP/s, 2 flops per FMA) from the
+    library's own microbenchmark kernels (libnnm_peaks.so), timed with CUDA events.
+    Each kernel runs about 50-100 ms; the clocks seen meanwhile are sampled."""
+    import ctypes
+
+    from paper_1402_3789_gb300 import build
+    build.build()
+    lib = ctypes.CDLL(build.peaks_library_path())
+    out = {}
+    import torch
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    time.sleep(0.3)
+    for name, fn, iters in (("fp32_tflops", lib.nnm_peak_fp32, 20000), ("fp64_tflops", lib.nnm_peak_fp64, 400)):
+        fn.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        fn.restype = ctypes.c_int
+        best = 0.0
+        for _ in range(3):
+            tf, ms = ctypes.c_double(), ctypes.c_double()
+            if fn(8, iters, ctypes.byref(tf), ctypes.byref(ms)) != 0:
+                break
+            if ms.value < 40.0:   # lengthen short runs so that launch overheads vanish
+                iters = int(iters * 60.0 / max(ms.value, 1e-3))
+                continue
+            best = max(best, tf.value)
+        out[name] = best
+    clocks = sampler.stop()
+    out["sm_mhz"] = clocks.get("sm_mhz")
+    out["method"] = ("own FMA-chain kernels (8 independent chains per thread, 8 blocks of 256 threads per SM), "
+                     "CUDA events, best of 3 runs of >= 40 ms; flops = 2 per FMA")
+    return out
+
+
 KERNEL_SOURCES = ["paper_1402_3789_gb300/csrc/sweep_tc.cu", "paper_1402_3789_gb300/csrc/select.cuh",
                   "paper_1402_3789_gb300/csrc/nnm_internal.cuh"]
 
@@ -256,6 +291,7 @@ def run_ours(args, world, rank, local):
         finally:
             nnm.nnm_destroy(ctx)
 
+    arith = measure_arith_peaks() if not args.no_peaks else {}
     for _ in range(args.warmup):
         step(args.precision)
     torch.cuda.synchronize()
@@ -285,21 +321,24 @@ def run_ours(args, world, rank, local):
     peaks, peak_kind = load_peaks()
     sweep_ms = statistics.mean(s["sweep_ms_per_launch_full"] for s in stats)
     # the work one launch does: the pairs of the tiles it evaluated (the bounding-sphere
-    # test skips the others); the whole matrix gives the effective rate beside it
+    # and landmark tests skip the others); the whole matrix gives the effective rate beside it
     sweep_pairs = statistics.mean(s["full_sweep_pairs_computed"] for s in stats)
     all_pairs = stats[-1]["full_sweep_pairs"]
-    per_pair = 3 * d if args.precision == "fp32" else 2 * stats[-1]["k_pad"]
+    kpad = stats[-1]["k_pad"]
+    kpad1 = 16 * ((d + 6 + 15) // 16)   # K of the one-term 16-bit form (32 at d = 25)
     if args.precision == "fp32":
-        flops = sweep_pairs * 3 * d
-        # FP32 CUDA cores: 152 SMs x 128 lanes x 2 flops (FMA) x clock under load
-        clk = (clocks.get("sm_mhz") or 1447.0) * 1e6
-        peak = 152 * 128 * 2 * clk / 1e12
-        roof = {"bound": "alu", "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock sampled"}
+        per_pair = 3 * d
+        peak = arith.get("fp32_tflops") or 152 * 128 * 2 * (clocks.get("sm_mhz") or 1447.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "peak_source": ("measured FP32 FMA throughput (own microbenchmark, "
+                                                f"{arith.get('sm_mhz')} MHz median)" if arith.get("fp32_tflops")
+                                                else "152 SMs x 128 FP32 lanes x 2 x median SM clock")}
     else:
-        kpad = stats[-1]["k_pad"]
-        flops = sweep_pairs * 2 * kpad
+        # the method's work per pair is one K = kpad1 product (2 kpad1 MMA flops); the split
+        # form issues 3x that on the tensor pipe for precision, reported as the pipe's occupancy
+        per_pair = 2 * kpad1
         peak = peaks.get("bf16_tflops_sustained", 1700.0)   # same rate for fp16 operands
         roof = {"bound": "tensor", "peak_source": f"bf16_tflops_sustained ({peak_kind})"}
+    flops = sweep_pairs * per_pair
     achieved = flops / (sweep_ms / 1e3) / 1e12
     traffic, traffic_src = captured_traffic(args.precision, N)
     if traffic is not None:
@@ -310,6 +349,20 @@ def run_ours(args, world, rank, local):
                  "pairs_per_launch": sweep_pairs, "pairs_full_matrix": all_pairs,
                  "effective_tflops_full_matrix": all_pairs * per_pair / (sweep_ms / 1e3) / 1e12,
                  "launch_ms": sweep_ms})
+    if args.precision != "fp32":
+        pipe = sweep_pairs * 2 * kpad / (sweep_ms / 1e3) / 1e12
+        roof.update({"tensor_pipe_flops_per_pair": 2 * kpad, "tensor_pipe_tflops": pipe,
+                     "tensor_pipe_frac": pipe / peak})
+    # the binary64 re-rank against the measured FP64 peak: 3d binary64 operations per
+    # re-ranked pair (d subtractions, d products, d additions)
+    rr_ms = statistics.mean(s["ms_rerank"] for s in stats)
+    rr_flops = statistics.mean(s["rerank_pairs"] for s in stats) * 3 * d
+    rerank_roof = {"bound": "fp64", "phase_ms": rr_ms, "fp64_flops": rr_flops,
+                   "achieved_tflops": rr_flops / (rr_ms / 1e3) / 1e12 if rr_ms > 0 else None,
+                   "peak_tflops": arith.get("fp64_tflops"),
+                   "note": "whole re-rank phase (selections, compaction and the binary64 distances)"}
+    if arith.get("fp64_tflops") and rr_ms > 0:
+        rerank_roof["frac"] = rerank_roof["achieved_tflops"] / arith["fp64_tflops"]
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -331,7 +384,7 @@ def run_ours(args, world, rank, local):
             "max_rel_err_vs_fp64": max(s["max_rel_err"] for s in stats),
             "n_merges": last.n_merges, "n_clusters": last.n_clusters,
             "kernel_rate_gpairs": stats[-1]["pairs_evaluated"] / 2 / (statistics.mean(s["ms_sweep"] for s in stats) / 1e3) / 1e9,
-            "roofline": roof, "clocks": clocks,
+            "roofline": roof, "rerank_roofline": rerank_roof, "peaks_measured": arith, "clocks": clocks,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats))}
 
     # the other precisions named by --compare, one timed step each after one untimed step
@@ -354,21 +407,28 @@ def run_ours(args, world, rank, local):
     if comp:
         line["compare"] = comp
 
-    # end to end through the public API from host memory
+    # end to end through the C ABI from host memory (nnm_cluster_host: the library copies X
+    # to the device, clusters, and copies merges and labels back); the page-locked host
+    # buffers are allocated before the timed region
     if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        mh = torch.empty(max(N - 1, 1) * 32, dtype=torch.uint8).pin_memory()
+        lh = torch.empty(N, dtype=torch.int32).pin_memory()
+        nnm.cluster_host(Xh, restr, precision=args.precision, merges_out=mh, labels_out=lh)
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         nm = 0
         for _ in range(args.steps):
-            merges, labels, K = nnm.cluster_host(X, restr, precision=args.precision)
+            merges, labels, K = nnm.cluster_host(Xh, restr, precision=args.precision, merges_out=mh, labels_out=lh)
             nm = merges.shape[0]
         t1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(t0.elapsed_time(t1), world) / args.steps
         line["e2e"] = {"value": world * pairs / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
-                       "h2d_bytes_per_step": N * d * 4, "d2h_bytes_per_step": N * 4 + nm * 32, "ms_per_step": e2e_ms}
+                       "h2d_bytes_per_step": N * d * 4, "d2h_bytes_per_step": N * 4 + nm * 32, "ms_per_step": e2e_ms,
+                       "api": "nnm_cluster_host (C ABI, page-locked host buffers)"}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         rate, R, dt, cores = oracle_pair_rate(X, args.cpu_seconds)

@@ -85,6 +85,12 @@ typedef struct {
     int32_t no_tile_pruning; /* 1: evaluate every column tile (no skipping by bounding
                                 spheres or landmark distances; results are identical,
                                 only slower)                                               */
+    int64_t wait_limit_ns; /* 0: 2 s.  Longest time one device-side wait of the tensor-core
+                              sweep (for a copied tile, an accumulator, a planned tile or a
+                              threshold) may take before the kernel gives up, raises its
+                              error flag and exits; the call then returns NNM_ETIMEOUT and
+                              the context stays usable.  1 .. 60e9 (larger is taken as 60 s);
+                              negative: EINVAL.  See nnm_set_wait_limit.                   */
 } nnm_options;
 
 /* Restrictions ("Problem statement"; "Problem settings").  Zero disables each one.
@@ -216,6 +222,27 @@ nnm_status nnm_nearest(nnm_ctx *ctx, int32_t k, uint32_t *idx_dev, double *D_dev
  * about 220 bytes per tree edge of scratch in the context (kept until nnm_destroy). */
 nnm_status nnm_cluster(nnm_ctx *ctx, const nnm_restrictions *restrictions, nnm_merge *merges_dev,
                        int64_t *n_merges_host, int32_t *labels_dev, int64_t *n_clusters_host);
+
+/* nnm_cluster_host -- nnm_create + nnm_cluster + nnm_destroy from and to host memory, for
+ * callers whose rows live on the host: X is copied to the device, clustered, and the
+ * merges and labels are copied back, all on cuda_stream.  The paper's program reads its
+ * records from host memory and writes its results back ("Objectives of the main module").
+ *   X_host          row-major float32 [N][d] host memory (page-locked memory copies
+ *                   fastest); read during the call only.
+ *   metric, precision, options   as for nnm_create;  restrictions  as for nnm_cluster.
+ *   merges_host     nnm_merge [N-1] host memory, written;  n_merges_host receives the count.
+ *   labels_host     int32 [N] host memory, written;  n_clusters_host receives K.
+ * The device memory the call needs (X, merges, labels and the context's workspace) is
+ * allocated and freed inside the call.  N >= 2.  Errors: those of nnm_create and
+ * nnm_cluster. */
+nnm_status nnm_cluster_host(const float *X_host, int64_t N, int32_t d, nnm_metric metric,
+                            nnm_precision precision, const nnm_options *options,
+                            const nnm_restrictions *restrictions, void *cuda_stream, nnm_merge *merges_host,
+                            int64_t *n_merges_host, int32_t *labels_host, int64_t *n_clusters_host);
+
+/* nnm_set_wait_limit -- change the context's wait limit (nnm_options.wait_limit_ns) for
+ * the calls that follow; 0 restores the 2 s default.  EINVAL if wait_limit_ns < 0. */
+nnm_status nnm_set_wait_limit(nnm_ctx *ctx, int64_t wait_limit_ns);
 
 /* nnm_get_tree -- copy the merge tree of the last nnm_cluster call (edges sorted by
  * key; N-1 of them unless freeze_at_cap stopped it early).

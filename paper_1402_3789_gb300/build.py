@@ -31,6 +31,8 @@ UNITS = [(f"sweep_fp32_d{D}", "sweep_fp32.cu", [f"-DNNM_SWEEP_FP32_D={D}"]) for 
     ("dendro", "dendro.cu", []),
     ("restrict_static", "restrict_static.cu", []),
 ]
+# the arithmetic-peak microbenchmarks (roofline denominators): a library of their own
+PEAK_UNITS = [("peaks", "peaks.cu", [])]
 
 
 def nvcc() -> str:
@@ -44,6 +46,10 @@ def library_path() -> str:
     return os.path.join(BUILD, "libnnm.so")
 
 
+def peaks_library_path() -> str:
+    return os.path.join(BUILD, "libnnm_peaks.so")
+
+
 def _sources_mtime() -> float:
     paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     paths.append(os.path.join(ROOT, "include", "nnm.h"))
@@ -53,7 +59,9 @@ def _sources_mtime() -> float:
 
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     out = library_path()
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= _sources_mtime():
+    peaks = peaks_library_path()
+    if (not force and os.path.exists(out) and os.path.exists(peaks)
+            and min(os.path.getmtime(out), os.path.getmtime(peaks)) >= _sources_mtime()):
         return out
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -62,9 +70,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if ptxas_info:
         common += ["-Xptxas", "-v"]
 
+    # a unit is recompiled when its object is older than its source, any header, this
+    # script, or when the build is forced
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    headers += [os.path.join(ROOT, "include", "nnm.h"), os.path.abspath(__file__)]
+    newest_header = max(os.path.getmtime(h) for h in headers)
+
     def compile_unit(unit):
         name, src, defs = unit
         obj = os.path.join(BUILD, name + ".o")
+        if (not force and os.path.exists(obj)
+                and os.path.getmtime(obj) >= max(newest_header, os.path.getmtime(os.path.join(CSRC, src)))):
+            return obj, ""
         cmd = [cc] + common + defs + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -72,18 +89,23 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj, r.stderr
 
     with cf.ThreadPoolExecutor(max_workers=min(len(UNITS), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(compile_unit, UNITS))
+        results = list(ex.map(compile_unit, UNITS + PEAK_UNITS))
     if verbose or ptxas_info:
         for _, err in results:
             if err:
                 sys.stderr.write(err)
-    tmp = out + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-rpath=/usr/local/cuda/lib64",
-                         "-o", tmp] + [o for o, _ in results]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, out)
+
+    def link(target, objs):
+        tmp = target + f".tmp{os.getpid()}"
+        cmd = [cc] + ARCH + ["-shared", "-cudart", "shared", "-Xlinker", "-rpath=/usr/local/cuda/lib64",
+                             "-o", tmp] + objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, target)
+
+    link(peaks, [o for o, _ in results[len(UNITS):]])
+    link(out, [o for o, _ in results[: len(UNITS)]])
     return out
 
 

@@ -40,6 +40,7 @@ struct nnm_ctx {
     int d = 0;
     nnm_precision prec = NNM_PREC_FP32;
     nnm_options opt{};
+    uint64_t wait_ns = 2000000000ull;   // device-side wait limit of the tensor-core sweep
     int64_t Npad = 0;
     int dp = 0;
     int kpad = 0;
@@ -202,6 +203,13 @@ struct Phase {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// nnm_options.wait_limit_ns -> nanoseconds (0: 2 s; at most 60 s)
+uint64_t wait_limit(int64_t ns)
+{
+    if (ns <= 0) return 2000000000ull;
+    return ns > 60000000000ll ? 60000000000ull : (uint64_t)ns;
+}
+
 bool is_tensor(const nnm_ctx *c) { return c->prec != NNM_PREC_FP32; }
 
 // Column ranges per row tile: enough CTAs to fill the 152 SMs a few times.
@@ -324,6 +332,7 @@ SweepArgs base_sweep(nnm_ctx *c)
     a.col_end = c->N;
     a.pos2row = c->pos2row;
     a.err_flag = &c->derr[0];
+    a.wait_ns = c->wait_ns;
     a.prune = c->opt.no_tile_pruning ? 0 : 1;
     a.tile_w = c->tile_w;
     a.tile_c = c->tile_c;
@@ -1007,7 +1016,9 @@ static nnm_status create_impl(const float *X_dev, int64_t N, int32_t d, const in
         precision != NNM_PREC_BF16X3_RERANK)
         return NNM_EUNSUPPORTED;
     if (precision == NNM_PREC_BF16X3_RERANK && d > 30) return NNM_EUNSUPPORTED;
-    if (options && (options->cache_k < 0 || options->cache_k > 16 || options->col_split < 0)) return NNM_EINVAL;
+    if (options && (options->cache_k < 0 || options->cache_k > 16 || options->col_split < 0 ||
+                    options->wait_limit_ns < 0))
+        return NNM_EINVAL;
     int64_t min_rows = N;
     if (offsets) {
         if (n_inst < 1 || n_inst > 65535 || offsets[0] != 0 || offsets[n_inst] != N) return NNM_EINVAL;
@@ -1024,6 +1035,7 @@ static nnm_status create_impl(const float *X_dev, int64_t N, int32_t d, const in
     c->metric = (int)metric;
     c->margin.metric = (int)metric;
     if (options) c->opt = *options;
+    c->wait_ns = wait_limit(c->opt.wait_limit_ns);
     c->stream = (cudaStream_t)cuda_stream;
     c->kc = c->opt.cache_k > 0 ? c->opt.cache_k : (precision == NNM_PREC_BF16_RERANK ? 2 : 8);
     if (c->kc > N - 1) c->kc = N > 1 ? (int)(N - 1) : 1;
@@ -1199,6 +1211,64 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
     *n_merges_host = (int64_t)h[0];
     *n_clusters_host = (int64_t)h[1];
     return read_stats(c);
+}
+
+nnm_status nnm_set_wait_limit(nnm_ctx *c, int64_t wait_limit_ns)
+{
+    if (!c) return NNM_EINVAL;
+    if (wait_limit_ns < 0) return fail(c, NNM_EINVAL, "negative wait limit");
+    c->opt.wait_limit_ns = wait_limit_ns;
+    c->wait_ns = wait_limit(wait_limit_ns);
+    return NNM_OK;
+}
+
+nnm_status nnm_cluster_host(const float *X_host, int64_t N, int32_t d, nnm_metric metric, nnm_precision precision,
+                            const nnm_options *options, const nnm_restrictions *restrictions, void *cuda_stream,
+                            nnm_merge *merges_host, int64_t *n_merges_host, int32_t *labels_host,
+                            int64_t *n_clusters_host)
+{
+    if (!X_host || !merges_host || !n_merges_host || !labels_host || !n_clusters_host) return NNM_EINVAL;
+    if (N < 2 || N >= (int64_t(1) << 31) || d < 1 || d > 32) return NNM_EINVAL;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float *X = nullptr;
+    nnm_merge *mg = nullptr;
+    int32_t *lab = nullptr;
+    nnm_ctx *ctx = nullptr;
+    nnm_status st = NNM_OK;
+    auto cuda_status = [](cudaError_t e) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? NNM_ENOMEM : NNM_ECUDA;
+    };
+    do {
+        cudaError_t e = cudaMalloc((void **)&X, (size_t)N * d * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&mg, (size_t)(N - 1) * sizeof(nnm_merge));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&lab, (size_t)N * sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemcpyAsync(X, X_host, (size_t)N * d * sizeof(float), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            break;
+        }
+        st = nnm_create(X, N, d, metric, precision, cuda_stream, options, &ctx);
+        if (st != NNM_OK) break;
+        int64_t nm = 0, K = 0;
+        st = nnm_cluster(ctx, restrictions, mg, &nm, lab, &K);
+        if (st != NNM_OK) break;
+        e = cudaMemcpyAsync(merges_host, mg, (size_t)nm * sizeof(nnm_merge), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(labels_host, lab, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = cuda_status(e);
+            break;
+        }
+        *n_merges_host = nm;
+        *n_clusters_host = K;
+    } while (0);
+    nnm_destroy(ctx);   // synchronises the stream before freeing
+    if (!ctx) cudaStreamSynchronize(s);
+    cudaFree(X);
+    cudaFree(mg);
+    cudaFree(lab);
+    return st;
 }
 
 nnm_status nnm_get_tree(nnm_ctx *c, nnm_edge *edges_dev, int64_t *n_edges_host)

@@ -116,8 +116,10 @@ struct SweepArgs {
     uint32_t *coll_cnt;       // per slot counters
     uint32_t *coll_j;         // [nslots][coll_cap]
     int64_t coll_cap;
-    // bounded waits of the tensor kernel
+    // bounded waits of the tensor kernel: a wait for work gives up after wait_ns
+    // nanoseconds and raises *err_flag (the call returns NNM_ETIMEOUT)
     int *err_flag;
+    uint64_t wait_ns;
     // tile pruning: bounding spheres of the column tiles (width tile_w positions) over
     // y = (x - mu_f) * scale_f, and the constants of the lower bound on candidate values
     int prune;

@@ -34,7 +34,11 @@ constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere
 constexpr int kMaxStages = 8;
 constexpr int kBandWide = 64;   // band slots per row for one-term BF16 (a wide band)
 constexpr int kStageStride = 36;   // floats per thread in the hit-staging area (16-byte rows, no bank conflicts)
-constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
+// Waits for work (stages, accumulators, plan entries, thresholds) give up after the
+// caller's limit (SweepArgs::wait_ns, 2 s by default).  The drain waits at the end --
+// copies and MMAs this CTA issued, which must land before its shared memory and TMEM
+// are released -- keep their own fixed bound, so a short limit never cuts them.
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -71,14 +75,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 // warp-wide operation (a lone waiting lane cost about a thousand cycles per wait).  Every
 // lane observes the completed phase itself (acquire).  Returns false if the wait gave up
 // (time-out, or another role of this CTA already aborted).
-__device__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+__device__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, volatile int *abort_flag, uint64_t wait_ns)
 {
     uint64_t t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
         if (it == 0) t0 = global_ns();
         if ((it & 15) == 15) {
-            const int give_up = __shfl_sync(0xffffffffu, (int)(*abort_flag != 0 || global_ns() - t0 > kWaitNs), 0);
+            const int give_up = __shfl_sync(0xffffffffu, (int)(*abort_flag != 0 || global_ns() - t0 > wait_ns), 0);
             if (give_up) return false;
         }
     }
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     __syncthreads();
     const uint32_t tmem = sh->tmem_base;
     volatile int *abort_flag = &sh->abort_flag;
+    const uint64_t wait_ns = a.wait_ns;
 
     if (warp == kProdWarp) {
         // Producer: takes the planned tiles in order and stages each into the B ring with
@@ -387,7 +392,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             const uint64_t t0 = global_ns();
             bool ok = true;
             while (((volatile int *)&sh->plan_head)[0] <= taken) {
-                if (*abort_flag || global_ns() - t0 > kWaitNs) {
+                if (*abort_flag || global_ns() - t0 > wait_ns) {
                     ok = false;
                     break;
                 }
@@ -404,7 +409,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             __syncwarp();
             if (lane == 0) ((volatile int *)&sh->plan_tail)[0] = taken + 1;
             const int s = issued % kStages;
-            if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag)) {
+            if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag, wait_ns)) {
                 *abort_flag = 1;
                 break;
             }
@@ -426,7 +431,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         if (lane == 0) {
             for (int q = issued - kStages < 0 ? 0 : issued - kStages; q < issued; ++q) {
                 const uint64_t t0 = global_ns();
-                while (!mbar_try_wait(&sh->full[q % kStages], (q / kStages) & 1) && global_ns() - t0 < kWaitNs)
+                while (!mbar_try_wait(&sh->full[q % kStages], (q / kStages) & 1) && global_ns() - t0 < kDrainNs)
                     __nanosleep(256);
             }
         }
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             const uint64_t t0 = global_ns();
             bool ok = true;
             while (planned - ((volatile int *)&sh->plan_tail)[0] >= kPlanQ) {
-                if (*abort_flag || global_ns() - t0 > kWaitNs) {
+                if (*abort_flag || global_ns() - t0 > wait_ns) {
                     ok = false;
                     break;
                 }
@@ -517,7 +522,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             if (ok_all && nblk > 0 && lane == 0) {
                 const uint64_t t0 = global_ns();
-                while (((volatile int *)&sh->npub)[0] < kEpiWarps && !*abort_flag && global_ns() - t0 < kWaitNs)
+                while (((volatile int *)&sh->npub)[0] < kEpiWarps && !*abort_flag && global_ns() - t0 < wait_ns)
                     __nanosleep(64);
             }
             __syncwarp();
@@ -583,8 +588,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         int done = 0;
         for (int q = 0;; ++q) {
             const int s = q % kStages, b = q & 1;
-            bool ok = mbar_wait_warp(&sh->full[s], (q / kStages) & 1, abort_flag);
-            if (ok && q >= 2) ok = mbar_wait_warp(&sh->tempty[b], ((q >> 1) - 1) & 1, abort_flag);
+            bool ok = mbar_wait_warp(&sh->full[s], (q / kStages) & 1, abort_flag, wait_ns);
+            if (ok && q >= 2) ok = mbar_wait_warp(&sh->tempty[b], ((q >> 1) - 1) & 1, abort_flag, wait_ns);
             if (!ok) {
                 *abort_flag = 1;
                 break;
@@ -623,7 +628,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         if (lane == 0 && done > 0) {
             mma_commit(&sh->drain);
             const uint64_t t0 = global_ns();
-            while (!mbar_try_wait(&sh->drain, 0) && global_ns() - t0 < kWaitNs) __nanosleep(256);
+            while (!mbar_try_wait(&sh->drain, 0) && global_ns() - t0 < kDrainNs) __nanosleep(256);
         }
         __syncwarp();
     } else {
@@ -710,7 +715,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         };
         for (int q = 0;; ++q) {
             const int b = q & 1;
-            if (!mbar_wait_warp(&sh->tfull[b], (q >> 1) & 1, abort_flag)) {
+            if (!mbar_wait_warp(&sh->tfull[b], (q >> 1) & 1, abort_flag, wait_ns)) {
                 *abort_flag = 1;
                 break;
             }

@@ -38,7 +38,8 @@ class NNMError(RuntimeError):
 
 class nnm_options(ctypes.Structure):
     _fields_ = [("cache_k", ctypes.c_int32), ("freeze_at_cap", ctypes.c_int32),
-                ("col_split", ctypes.c_int32), ("no_tile_pruning", ctypes.c_int32)]
+                ("col_split", ctypes.c_int32), ("no_tile_pruning", ctypes.c_int32),
+                ("wait_limit_ns", ctypes.c_int64)]
 
 
 class nnm_restrictions(ctypes.Structure):
@@ -62,7 +63,8 @@ class nnm_stats(ctypes.Structure):
 
 # every symbol include/nnm.h declares
 EXPORTS = ("nnm_create", "nnm_create_batched", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats",
-           "nnm_last_error", "nnm_status_string", "nnm_destroy", "nnm_restrict_static")
+           "nnm_last_error", "nnm_status_string", "nnm_destroy", "nnm_restrict_static", "nnm_cluster_host",
+           "nnm_set_wait_limit")
 STATIC_MAX_ROWS = 1 << 20
 
 _LIB = None
@@ -108,6 +110,12 @@ def load_library(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.nnm_restrict_static.argtypes = [P, i64, i64, ctypes.c_int, ctypes.POINTER(nnm_restrictions), P,
                                         ctypes.POINTER(i64), P, ctypes.POINTER(i64), P]
     lib.nnm_restrict_static.restype = ctypes.c_int
+    lib.nnm_cluster_host.argtypes = [P, i64, i32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(nnm_options),
+                                     ctypes.POINTER(nnm_restrictions), P, P, ctypes.POINTER(i64), P,
+                                     ctypes.POINTER(i64)]
+    lib.nnm_cluster_host.restype = ctypes.c_int
+    lib.nnm_set_wait_limit.argtypes = [P, i64]
+    lib.nnm_set_wait_limit.restype = ctypes.c_int
     _LIB = lib
     return lib
 
@@ -141,14 +149,15 @@ METRICS = {"euclidean": 0, "manhattan": 1, "chebyshev": 2}
 
 def nnm_create(X: torch.Tensor, precision: str = "fp32", stream: torch.cuda.Stream | None = None,
                cache_k: int = 0, freeze_at_cap: bool = False, col_split: int = 0,
-               tile_pruning: bool = True, metric: str = "euclidean") -> Context:
+               tile_pruning: bool = True, metric: str = "euclidean", wait_limit_ns: int = 0) -> Context:
     """nnm_create: X is a contiguous float32 [N, d] CUDA tensor (kept alive by the context)."""
     lib = load_library()
     if not (isinstance(X, torch.Tensor) and X.is_cuda and X.dtype == torch.float32 and X.dim() == 2):
         raise ValueError("X must be a float32 [N, d] CUDA tensor")
     X = X.contiguous()
     stream = stream or torch.cuda.current_stream(X.device)
-    opt = nnm_options(int(cache_k), int(bool(freeze_at_cap)), int(col_split), int(not tile_pruning))
+    opt = nnm_options(int(cache_k), int(bool(freeze_at_cap)), int(col_split), int(not tile_pruning),
+                      int(wait_limit_ns))
     h = ctypes.c_void_p()
     st = lib.nnm_create(ctypes.c_void_p(X.data_ptr()), X.shape[0], X.shape[1], METRICS[metric], PRECISIONS[precision],
                         ctypes.c_void_p(stream.cuda_stream), ctypes.byref(opt), ctypes.byref(h))
@@ -187,9 +196,9 @@ def nnm_create_batched(Xs, precision: str = "fp32", stream: torch.cuda.Stream | 
 
 
 def nnm_nearest(ctx: Context, k: int):
-    """Exact k nearest neighbours of every row: (idx int32 [N,k], D float64 [N,k]) on the device."""
+    """Exact k nearest neighbours of every row: (idx uint32 [N,k], D float64 [N,k]) on the device."""
     lib = load_library()
-    idx = torch.empty((ctx.N, k), dtype=torch.int32, device=ctx.X.device)
+    idx = torch.empty((ctx.N, k), dtype=torch.int32, device=ctx.X.device).view(torch.uint32)
     D = torch.empty((ctx.N, k), dtype=torch.float64, device=ctx.X.device)
     ctx._check(lib.nnm_nearest(ctx.handle, k, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(D.data_ptr())))
     return idx, D
@@ -276,15 +285,39 @@ def nnm_status_string(status: int) -> str:
     return load_library().nnm_status_string(status).decode()
 
 
-def cluster_host(X: np.ndarray, restrictions=None, precision: str = "fp32", device: str = "cuda", **options):
-    """End to end from host memory: pinned host -> device copy, nnm_create, nnm_cluster,
-    and the labels and merges copied back.  Returns (merges, labels, n_clusters)."""
-    Xh = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).pin_memory()
-    Xd = Xh.to(device, non_blocking=True)
-    ctx = nnm_create(Xd, precision=precision, **options)
-    try:
-        res = nnm_cluster(ctx, restrictions)
-        labels = res.labels.cpu().numpy()
-        return res.merges(), labels, res.n_clusters
-    finally:
-        nnm_destroy(ctx)
+def nnm_set_wait_limit(ctx: Context, wait_limit_ns: int) -> None:
+    """Wait limit of the tensor-core sweep's device-side waits for the following calls
+    (0: the 2 s default)."""
+    ctx._check(load_library().nnm_set_wait_limit(ctx.handle, int(wait_limit_ns)))
+
+
+def cluster_host(X, restrictions=None, precision: str = "fp32", metric: str = "euclidean", merges_out=None,
+                 labels_out=None, stream: torch.cuda.Stream | None = None, **options):
+    """nnm_cluster_host: end to end from host memory through the C ABI (the library
+    copies X to the device, clusters, and copies merges and labels back).  X is a
+    float32 [N, d] numpy array or CPU tensor (page-locked copies fastest); merges_out /
+    labels_out may be preallocated CPU tensors (uint8 [(N-1)*32], int32 [N]).
+    Returns (merges, labels, n_clusters) as numpy arrays."""
+    lib = load_library()
+    Xh = X if isinstance(X, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32))
+    if Xh.is_cuda or Xh.dtype != torch.float32 or Xh.dim() != 2:
+        raise ValueError("X must be a float32 [N, d] host array")
+    Xh = Xh.contiguous()
+    N, d = Xh.shape
+    merges = merges_out if merges_out is not None else torch.empty(max(N - 1, 1) * MERGE_DTYPE.itemsize,
+                                                                    dtype=torch.uint8)
+    labels = labels_out if labels_out is not None else torch.empty(N, dtype=torch.int32)
+    opt = nnm_options(int(options.get("cache_k", 0)), int(bool(options.get("freeze_at_cap", False))),
+                      int(options.get("col_split", 0)), int(not options.get("tile_pruning", True)),
+                      int(options.get("wait_limit_ns", 0)))
+    r = _restrictions(restrictions)
+    stream = stream or torch.cuda.current_stream()
+    n_m, n_c = ctypes.c_int64(), ctypes.c_int64()
+    st = lib.nnm_cluster_host(ctypes.c_void_p(Xh.data_ptr()), N, d, METRICS[metric], PRECISIONS[precision],
+                              ctypes.byref(opt), ctypes.byref(r), ctypes.c_void_p(stream.cuda_stream),
+                              ctypes.c_void_p(merges.data_ptr()), ctypes.byref(n_m),
+                              ctypes.c_void_p(labels.data_ptr()), ctypes.byref(n_c))
+    if st != NNM_OK:
+        raise NNMError(st, "nnm_cluster_host failed")
+    # views of the output buffers (the caller's, when given): no extra host copy
+    return merges[: n_m.value * MERGE_DTYPE.itemsize].numpy().view(MERGE_DTYPE), labels.numpy(), n_c.value

@@ -28,7 +28,7 @@ def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
     assert set(names) == {"nnm_create", "nnm_nearest", "nnm_cluster", "nnm_get_tree", "nnm_get_stats",
                           "nnm_last_error", "nnm_status_string", "nnm_destroy", "nnm_restrict_static",
-                          "nnm_create_batched"}
+                          "nnm_create_batched", "nnm_cluster_host", "nnm_set_wait_limit"}
     for n in names:
         assert hasattr(lib, n), n
     from paper_1402_3789_gb300 import nnm
