@@ -103,9 +103,15 @@ typedef struct {
  *   kl4_min_size       KL4: joins that touch a cluster with fewer than KL4 rows go
  *                      first: one pass in key order makes only those joins and defers
  *                      the rest, a second pass in key order handles the deferred ones.
- *   semantics          0: the gates act on the merge-tree edges in key order (the only
- *                      value this build accepts; 1, gates on every pair, is rejected
- *                      with NNM_EUNSUPPORTED).
+ *   semantics          0: the gates act on the merge-tree edges in key order (tree
+ *                      semantics, the default).  1: the gates act on every pair in key
+ *                      order, as the paper's batched procedure over all pairs walks them
+ *                      ("General description of the algorithm for constructing the set
+ *                      of minimum distances"); with KL2 or KL3 a cluster may then join
+ *                      through a pair that is not a tree edge.  Semantics 1 costs O(N^2)
+ *                      pair evaluations per batch of joins and takes one instance of at
+ *                      most 262,144 rows (else NNM_EUNSUPPORTED); the tree is not built.
+ *                      Other values: NNM_EINVAL.
  * A join blocked by a gate is not retried (sizes only grow). */
 typedef struct {
     double max_join_dist;
@@ -211,7 +217,8 @@ nnm_status nnm_nearest(nnm_ctx *ctx, int32_t k, uint32_t *idx_dev, double *D_dev
 /* nnm_cluster -- the NNM merge tree (single linkage, minimum spanning tree under
  * key order) and the restricted joins on it.
  *   restrictions  may be NULL (no restriction).  EINVAL: negative values, KL3 <= KL2
- *                 with both set (the paper takes KL3 above KL2); EUNSUPPORTED: semantics != 0.
+ *                 with both set (the paper takes KL3 above KL2), semantics not 0 or 1;
+ *                 EUNSUPPORTED: semantics 1 beyond its limits (see nnm_restrictions).
  *   merges_dev    nnm_merge [N-1] device, the accepted joins in acceptance order.
  *   n_merges_host receives their number.
  *   labels_dev    int32 [N] device: cluster of every row, 0..K-1, numbered by each
@@ -283,7 +290,8 @@ void nnm_destroy(nnm_ctx *ctx);
  *   metric         the metric the tree's D values are in (the context's metric): it fixes
  *                  the cap's units and the merges' reported length, as for nnm_cluster;
  *                  an unknown value gives NNM_EINVAL.
- *   restrictions   as for nnm_cluster (may be NULL); same EINVAL / EUNSUPPORTED rules.
+ *   restrictions   as for nnm_cluster (may be NULL); same EINVAL rules; semantics 1 (which
+ *                  needs the rows, not a tree) gives NNM_EUNSUPPORTED.
  *   merges_dev, n_merges_host, labels_dev, n_clusters_host  as for nnm_cluster.
  *   cuda_stream    cudaStream_t to enqueue on (NULL: the legacy default stream); the call
  *                  returns after its work has completed.

@@ -30,6 +30,7 @@ UNITS = [(f"sweep_fp32_d{D}", "sweep_fp32.cu", [f"-DNNM_SWEEP_FP32_D={D}"]) for 
     ("restrict", "restrict.cu", []),
     ("dendro", "dendro.cu", []),
     ("restrict_static", "restrict_static.cu", []),
+    ("literal", "literal.cu", []),
 ]
 # the arithmetic-peak microbenchmarks (roofline denominators): a library of their own
 PEAK_UNITS = [("peaks", "peaks.cu", [])]

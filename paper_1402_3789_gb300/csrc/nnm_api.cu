@@ -238,6 +238,20 @@ nnm_status ensure_cand(nnm_ctx *c, size_t records)
     return NNM_OK;
 }
 
+uint32_t float_bits(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+
+float bits_float(uint32_t u)
+{
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 // float >= x (round up)
 float up_f(double x)
 {
@@ -984,6 +998,266 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     return NNM_OK;
 }
 
+constexpr int64_t kLiteralMaxRows = 262144;
+
+// Device buffers of one call, freed when it returns.
+struct CallScratch {
+    std::vector<void *> ptrs;
+    template <typename T>
+    cudaError_t get(T **p, size_t count)
+    {
+        *p = nullptr;
+        cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            return e;
+        }
+        ptrs.push_back(*p);
+        return cudaSuccess;
+    }
+    void release(void *p)
+    {
+        for (auto &q : ptrs)
+            if (q == p) {
+                cudaFree(q);
+                q = nullptr;
+            }
+    }
+    ~CallScratch()
+    {
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+};
+
+float down_f(double x)
+{
+    float f = (float)x;
+    if ((double)f > x) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+// The restrictions in the paper's all-pairs reading (semantics = 1): batches of the pairs
+// that cross two clusters and pass every gate at the batch start, each complete for a
+// key range above the last one, walked in key order (literal.cu has the argument).  Two
+// phases with KL4.  The tree is not needed; the labels come from the walk's union-find.
+nnm_status cluster_literal(nnm_ctx *c, const nnm_restrictions &r, double cap2, nnm_merge *merges_dev,
+                           int64_t *n_merges_host, int32_t *labels_dev, int64_t *n_clusters_host)
+{
+    if (c->n_inst > 1) return fail(c, NNM_EUNSUPPORTED, "the all-pairs reading (semantics 1) takes one instance");
+    if (c->N > kLiteralMaxRows)
+        return fail(c, NNM_EUNSUPPORTED, "the all-pairs reading (semantics 1) takes N <= %lld", (long long)kLiteralMaxRows);
+    const int64_t N = c->N;
+    cudaStream_t s = c->stream;
+    CallScratch sc;
+    LitArgs a{};
+    a.X = c->X;
+    a.d = c->d;
+    a.N = N;
+    a.metric = c->metric;
+    a.cap2 = cap2;
+    a.cap2f = cap2 < INFINITY ? up_f(cap2) : INFINITY;
+    a.kl2 = r.kl2_max_pre_size;
+    a.kl3 = r.kl3_max_size;
+    a.kl4 = r.kl4_min_size;
+    a.c0 = c->selc.c0_32;
+    a.c1 = c->selc.c1_32;
+    a.c1inv = down_f(1.0 / (double)a.c1);
+    const int fine_bins = literal_fine_bins();
+    unsigned long long *cnt = nullptr;   // [0] emitted [1] kept [2] merges [3] K
+    long long *joined = nullptr;
+    int *stop = nullptr;
+    uint32_t *minm = nullptr, *lflag = nullptr, *bsums = nullptr;
+    cudaError_t e = sc.get(&a.uf_parent, N);
+    if (e == cudaSuccess) e = sc.get(&a.uf_size, N);
+    if (e == cudaSuccess) e = sc.get(&a.comp, N);
+    if (e == cudaSuccess) e = sc.get(&a.csize, N);
+    if (e == cudaSuccess) e = sc.get(&a.tD, N);
+    if (e == cudaSuccess) e = sc.get(&a.tab, N);
+    if (e == cudaSuccess) e = sc.get(&a.w0, N);
+    if (e == cudaSuccess) e = sc.get(&a.w1, N);
+    if (e == cudaSuccess) e = sc.get(&a.w2, N);
+    if (e == cudaSuccess) e = sc.get(&a.w3, N);
+    if (e == cudaSuccess) e = sc.get(&a.w4, N);
+    if (e == cudaSuccess) e = sc.get(&a.hist, (size_t)fine_bins);
+    if (e == cudaSuccess) e = sc.get(&cnt, 4);
+    if (e == cudaSuccess) e = sc.get(&joined, 1);
+    if (e == cudaSuccess) e = sc.get(&stop, 1);
+    if (e == cudaSuccess) e = sc.get(&minm, N);
+    if (e == cudaSuccess) e = sc.get(&lflag, N);
+    if (e == cudaSuccess) e = sc.get(&bsums, (size_t)labels_scratch_blocks(N));
+    if (e != cudaSuccess) return fail(c, NNM_ENOMEM, "all-pairs reading: scratch allocation failed");
+    a.n_emit = &cnt[0];
+    a.n_kept = &cnt[1];
+    NNM_CUDA(c, cudaMemsetAsync(cnt, 0, 4 * sizeof(unsigned long long), s));
+    NNM_CUDA(c, cudaMemsetAsync(joined, 0, sizeof(long long), s));
+    NNM_CUDA(c, cudaMemsetAsync(stop, 0, sizeof(int), s));
+    NNM_CUDA(c, launch_lit_init(a, a.kl4 > 0 ? INFINITY : -1.0, s));
+    // pairs per batch: large enough that the all-pairs passes stay a small share
+    int64_t P = 8 * N;
+    if (P < (int64_t(1) << 20)) P = int64_t(1) << 20;
+    if (P > (int64_t(1) << 24)) P = int64_t(1) << 24;
+    int64_t cap = 0;
+    nnm_edge *tmp = nullptr;
+    std::vector<unsigned long long> h(fine_bins);
+    const double c0 = a.c0, c1inv = a.c1inv;
+    // tau(E): every pair with D <= tau has an FP32 value <= E
+    auto tau_of = [&](float E) -> double {
+        if (!(E < INFINITY)) return INFINITY;
+        double t = ((double)E - c0) * c1inv - c0;
+        t = nextafter(t, -INFINITY);
+        return t > 0.0 ? t : 0.0;
+    };
+    for (int phase = a.kl4 > 0 ? 1 : 2; phase <= 2; ++phase) {
+        int hstop = 0;
+        NNM_CUDA(c, cudaMemcpyAsync(&hstop, stop, sizeof(int), cudaMemcpyDeviceToHost, s));
+        NNM_CUDA(c, cudaStreamSynchronize(s));
+        if (hstop) break;
+        if (phase == 2 && a.kl4 > 0) {
+            unsigned long long n1 = 0;
+            NNM_TRY(read_dev(c, &n1, &cnt[2]));
+            NNM_CUDA(c, launch_lit_reach(a, merges_dev, (int64_t)n1, s));
+        }
+        a.phase = phase;
+        a.have_last = 0;
+        a.last_D = -INFINITY;
+        for (int batch = 0;; ++batch) {
+            if (batch > (1 << 20)) return fail(c, NNM_ECUDA, "all-pairs reading did not converge");
+            NNM_CUDA(c, launch_lit_flatten(a, s));
+            NNM_CUDA(c, cudaMemsetAsync(a.hist, 0, 256 * sizeof(unsigned long long), s));
+            NNM_CUDA(c, launch_lit_pass(a, 0, s));
+            NNM_CUDA(c, cudaMemcpyAsync(h.data(), a.hist, 256 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+            NNM_CUDA(c, cudaStreamSynchronize(s));
+            unsigned long long total = 0;
+            for (int q = 0; q < 256; ++q) total += h[q];
+            if (total == 0) break;
+            // the smallest cut that moves past the last batch
+            float Emin = 0.0f;
+            if (a.have_last) {
+                Emin = up_f((a.last_D + c0) / c1inv + c0);
+                Emin = nextafterf(Emin, INFINITY);
+            }
+            const unsigned emin_oct = a.have_last ? (unsigned)(float_bits(Emin) >> 23) : 0u;
+            unsigned oct = 0, last_nz = 0;
+            unsigned long long cum = 0, below = 0;
+            bool found = false;
+            for (unsigned q = 0; q < 256; ++q) {
+                if (h[q]) last_nz = q;
+                if (!found && cum + h[q] >= (unsigned long long)P) {
+                    oct = q;
+                    found = true;
+                }
+                if (!found) cum += h[q];
+            }
+            if (!found) oct = last_nz;
+            if (oct < emin_oct) oct = emin_oct;
+            below = 0;
+            for (unsigned q = 0; q < oct && q < 256; ++q) below += h[q];
+            float E;
+            unsigned long long count;
+            if (oct >= 255) {
+                E = INFINITY;
+                count = total;
+            } else {
+                NNM_CUDA(c, cudaMemsetAsync(a.hist, 0, (size_t)fine_bins * sizeof(unsigned long long), s));
+                a.octave = oct;
+                NNM_CUDA(c, launch_lit_pass(a, 1, s));
+                NNM_CUDA(c, cudaMemcpyAsync(h.data(), a.hist, (size_t)fine_bins * sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, s));
+                NNM_CUDA(c, cudaStreamSynchronize(s));
+                unsigned b = (unsigned)fine_bins - 1, fnz = 0;
+                bool fb = false;
+                unsigned long long fc = below;
+                for (unsigned q = 0; q < (unsigned)fine_bins; ++q) {
+                    if (h[q]) fnz = q;
+                    if (!fb && fc + h[q] >= (unsigned long long)P) {
+                        b = q;
+                        fb = true;
+                    }
+                    fc += h[q];
+                }
+                if (!fb) b = fnz;
+                if (oct == emin_oct && a.have_last) {
+                    const unsigned bmin = (float_bits(Emin) >> 11) & (unsigned)(fine_bins - 1);
+                    if (b < bmin) b = bmin;
+                }
+                E = bits_float((oct << 23) | (b << 11) | 0x7FFu);
+                count = below;
+                for (unsigned q = 0; q <= b; ++q) count += h[q];
+            }
+            const double tau = tau_of(E);
+            if (a.have_last && !(tau > a.last_D)) return fail(c, NNM_ECUDA, "all-pairs reading: no progress");
+            if (count > (unsigned long long)cap) {
+                if (a.emit) sc.release(a.emit);
+                if (a.kept) sc.release(a.kept);
+                if (tmp) sc.release(tmp);
+                cap = (int64_t)count;
+                if (sc.get(&a.emit, (size_t)cap) != cudaSuccess || sc.get(&a.kept, (size_t)cap) != cudaSuccess ||
+                    sc.get(&tmp, (size_t)cap) != cudaSuccess)
+                    return fail(c, NNM_ENOMEM, "all-pairs reading: %llu pairs in one batch", count);
+            }
+            a.emit_cap = cap;
+            a.cut = E;
+            a.tau_D = tau;
+            NNM_CUDA(c, cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), s));
+            NNM_CUDA(c, launch_lit_pass(a, 2, s));
+            unsigned long long ne = 0;
+            NNM_TRY(read_dev(c, &ne, &cnt[0]));
+            if (ne > (unsigned long long)cap) return fail(c, NNM_ECUDA, "all-pairs reading: emitted more than counted");
+            a.n_emitted = (int64_t)ne;
+            NNM_CUDA(c, launch_lit_exact(a, s));
+            unsigned long long nk = 0;
+            NNM_TRY(read_dev(c, &nk, &cnt[1]));
+            if (nk > 0) {
+                nnm_edge *sorted = nullptr;
+                NNM_CUDA(c, launch_sort_edges(a.kept, tmp, (int64_t)nk, s, &sorted));
+                RestrictArgs ra{};
+                ra.edges = sorted;
+                ra.m = (int64_t)nk;
+                ra.N = N;
+                ra.cap2 = cap2;
+                ra.kl1 = r.kl1_stop_clusters;
+                ra.kl2 = r.kl2_max_pre_size;
+                ra.kl3 = r.kl3_max_size;
+                ra.kl4 = r.kl4_min_size;
+                ra.uf_parent = a.uf_parent;
+                ra.uf_size = a.uf_size;
+                ra.merges = merges_dev;
+                ra.n_merges = &cnt[2];
+                ra.metric = c->metric;
+                ra.n_inst = 1;
+                ra.persist = 1;
+                ra.lit_phase = phase;
+                ra.joined_io = joined;
+                ra.stop_io = stop;
+                NNM_CUDA(c, launch_restrict(ra, s));
+                int hs = 0;
+                NNM_TRY(read_dev(c, &hs, stop));
+                if (hs) break;
+            }
+            a.have_last = 1;
+            a.last_D = tau;
+            if (!(tau < INFINITY)) break;
+        }
+    }
+    LabelArgs la{};
+    la.N = N;
+    la.uf_parent = a.uf_parent;
+    la.minm = minm;
+    la.flag = lflag;
+    la.block_sums = bsums;
+    la.labels = labels_dev;
+    la.K = &cnt[3];
+    NNM_CUDA(c, launch_labels(la, s));
+    unsigned long long hk[2];
+    NNM_CUDA(c, cudaMemcpyAsync(hk, &cnt[2], sizeof hk, cudaMemcpyDeviceToHost, s));
+    NNM_CUDA(c, cudaStreamSynchronize(s));
+    *n_merges_host = (int64_t)hk[0];
+    *n_clusters_host = (int64_t)hk[1];
+    return NNM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1112,8 +1386,7 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
     if (c->N < 2) return fail(c, NNM_EINVAL, "nnm_cluster needs N >= 2");
     nnm_restrictions r{};
     if (restr) r = *restr;
-    if (r.semantics == 1) return fail(c, NNM_EUNSUPPORTED, "paper-literal semantics (1) is not provided");
-    if (r.semantics != 0) return fail(c, NNM_EINVAL, "semantics must be 0");
+    if (r.semantics != 0 && r.semantics != 1) return fail(c, NNM_EINVAL, "semantics must be 0 or 1");
     if (isnan(r.max_join_dist) || r.kl1_stop_clusters < 0 || r.kl2_max_pre_size < 0 || r.kl3_max_size < 0 ||
         r.kl4_min_size < 0)
         return fail(c, NNM_EINVAL, "negative restriction");
@@ -1124,6 +1397,14 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
                             ? (c->metric == NNM_EUCLIDEAN ? r.max_join_dist * r.max_join_dist : r.max_join_dist)
                             : INFINITY;
     reset_stats(c);
+    if (r.semantics == 1) {
+        {
+            Phase total(c, &c->stats.ms_total);
+            Phase ph(c, &c->stats.ms_restrict);
+            NNM_TRY(cluster_literal(c, r, cap2, merges_dev, n_merges_host, labels_dev, n_clusters_host));
+        }
+        return read_stats(c);
+    }
     {
         Phase total(c, &c->stats.ms_total);
         NNM_TRY(build_tree(c, c->opt.freeze_at_cap ? cap2 : INFINITY));

@@ -410,6 +410,15 @@ struct RestrictArgs {
     const int64_t *ebeg, *eend;
     unsigned long long *inst_nm;   // [n_inst + 1] scratch
     nnm_merge *merges_tmp;         // [m] scratch
+    // the all-pairs reading (literal.cu): one walk over a key-sorted batch of pairs that
+    // continues the union-find, the merges, the join count and the KL1 stop of the batches
+    // before it (persist = 1: no initialisation; merges appended at *n_merges; *joined_io
+    // and *stop_io carried in and out).  lit_phase 1 skips a pair whose clusters both
+    // have at least KL4 rows (it waits for the second phase); 2 applies no KL4 test.
+    int persist;
+    int lit_phase;
+    long long *joined_io;
+    int *stop_io;
 };
 
 cudaError_t launch_restrict(const RestrictArgs &a, cudaStream_t s);
@@ -445,6 +454,44 @@ struct CutArgs {
 int64_t cut_hash_slots(int64_t m);
 // Returns after one synchronisation (the accepted count decides the levels).
 cudaError_t launch_restrict_cut(const CutArgs &a, int64_t *n_merges_host, cudaStream_t s);
+
+// The restrictions in the all-pairs reading (literal.cu): batches of pairs that cross two
+// clusters and pass every gate at the batch start, cut by FP32 value and kept exactly.
+struct LitArgs {
+    const float *X;            // the caller's rows [N][d]
+    int d;
+    int64_t N;
+    int metric;
+    double cap2;               // cap in D units (inf: none)
+    float cap2f;               // an FP32 value >= cap2
+    int64_t kl2, kl3, kl4;
+    int phase;                 // 1: pairs touching a cluster below KL4 only; 2: the rest
+    uint32_t *uf_parent, *uf_size;       // [N] union-find of the walk
+    uint32_t *comp, *csize;              // [N] per row: root and its size at the batch start
+    double *tD;                          // [N] per row: key of the phase-1 join that brought
+    unsigned long long *tab;             //     its cluster to KL4 rows (D, a << 32 | b)
+    uint32_t *w0, *w1, *w2, *w3, *w4;    // [N] scratch of k_lit_reach
+    float c0, c1, c1inv;       // FP32 margin: D <= (s + c0) c1 + c0, D >= (s - c0) c1inv - c0
+    int have_last;             // 0 before the first batch of a phase
+    double last_D;             // the previous batch covered every pair with D <= last_D
+    double tau_D;              // this batch: pairs with last_D < D <= tau_D
+    unsigned int octave;       // fine histogram: the FP32 exponent field it refines
+    float cut;                 // emit: pairs with FP32 value <= cut
+    unsigned long long *hist;  // [256] (by exponent) or [literal_fine_bins()]
+    nnm_edge *emit;            // [emit_cap] emitted pairs
+    int64_t emit_cap;
+    unsigned long long *n_emit;
+    int64_t n_emitted;
+    nnm_edge *kept;            // [emit_cap] pairs kept by the binary64 test
+    unsigned long long *n_kept;
+};
+int literal_fine_bins();
+// mode 0: histogram by exponent; 1: histogram of one octave; 2: emit up to the cut
+cudaError_t launch_lit_pass(const LitArgs &a, int mode, cudaStream_t s);
+cudaError_t launch_lit_exact(const LitArgs &a, cudaStream_t s);
+cudaError_t launch_lit_flatten(const LitArgs &a, cudaStream_t s);
+cudaError_t launch_lit_init(const LitArgs &a, double t0, cudaStream_t s);
+cudaError_t launch_lit_reach(const LitArgs &a, const nnm_merge *merges, int64_t n1, cudaStream_t s);
 
 struct LabelArgs {
     int64_t N;

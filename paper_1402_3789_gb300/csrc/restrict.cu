@@ -155,9 +155,11 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
     nnm_merge *merges = batched ? a.merges_tmp + elo : a.merges;
     uint32_t *deferred = a.deferred + elo;
 
-    for (int64_t i = rlo + t; i < rhi; i += kWalkThreads) {
-        a.uf_parent[i] = (uint32_t)i;
-        a.uf_size[i] = 1u;
+    if (!a.persist) {
+        for (int64_t i = rlo + t; i < rhi; i += kWalkThreads) {
+            a.uf_parent[i] = (uint32_t)i;
+            a.uf_size[i] = 1u;
+        }
     }
     if (t == 0) {
         // admissible prefix: the edges are key-sorted, so D <= cap^2 is a prefix
@@ -169,15 +171,16 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
         }
         m_adm = lo;
         n_def = 0;
-        n_out = 0;
-        S.stop = 0;
-        S.joined = 0;
+        n_out = a.persist ? (int64_t)*a.n_merges : 0;
+        S.stop = a.persist ? *a.stop_io : 0;
+        S.joined = a.persist ? (int64_t)*a.joined_io : 0;
     }
     __syncthreads();
 
-    const int walks = a.kl4 > 0 ? 2 : 1;
+    const int walks = (a.kl4 > 0 && !a.persist) ? 2 : 1;
     for (int walk = 0; walk < walks && !S.stop; ++walk) {
-        const bool defer_pass = a.kl4 > 0 && walk == 0;
+        const bool defer_pass = a.kl4 > 0 && walk == 0 && !a.persist;
+        const bool skip_big = a.persist && a.lit_phase == 1 && a.kl4 > 0;
         const int64_t total = walk == 0 ? m_adm : n_def;
         for (int64_t c0 = 0; c0 < total && !S.stop; c0 += kChunk) {
             const int n = (int)(total - c0 < kChunk ? total - c0 : kChunk);
@@ -229,8 +232,8 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
                     const uint32_t x = lfind(S.lpar, S.la[e]), y = lfind(S.lpar, S.lb[e]);
                     if (x == y) continue;
                     const uint32_t sx = S.lsize[x], sy = S.lsize[y];
-                    if (defer_pass && sx >= (uint64_t)a.kl4 && sy >= (uint64_t)a.kl4) {
-                        S.dec[e] = 2;
+                    if ((defer_pass || skip_big) && sx >= (uint64_t)a.kl4 && sy >= (uint64_t)a.kl4) {
+                        S.dec[e] = skip_big ? 0 : 2;
                         continue;
                     }
                     if (a.kl2 > 0 && (sx > (uint64_t)a.kl2 || sy > (uint64_t)a.kl2)) continue;
@@ -287,6 +290,10 @@ __global__ void __launch_bounds__(kWalkThreads, 1) k_restrict(const RestrictArgs
     if (t == 0) {
         if (batched) a.inst_nm[blockIdx.x] = (unsigned long long)n_out;
         else *a.n_merges = (unsigned long long)n_out;
+        if (a.persist) {
+            *a.joined_io = (long long)S.joined;
+            *a.stop_io = S.stop;
+        }
     }
 }
 

@@ -264,8 +264,8 @@ def test_errors(nnm):
             nnm.nnm_cluster(ctx, {"kl1_stop_clusters": -1})
         assert e.value.status == nnm.NNM_EINVAL
         with pytest.raises(nnm.NNMError) as e:
-            nnm.nnm_cluster(ctx, {"semantics": 1})
-        assert e.value.status == nnm.NNM_EUNSUPPORTED
+            nnm.nnm_cluster(ctx, {"semantics": 3})
+        assert e.value.status == nnm.NNM_EINVAL
         # the context stays usable after rejected calls
         idx, D = nnm.nnm_nearest(ctx, 2)
         assert idx.shape == (100, 2)
