@@ -58,6 +58,7 @@ struct nnm_ctx {
     uint32_t *inst_pos = nullptr;  // device [N]: instance of each position (and row)
     int64_t *ebeg = nullptr, *eend = nullptr;   // edge range of each instance in the tree
     unsigned long long *inst_nm = nullptr;      // merges per instance (restriction walks)
+    uint32_t *inst_edges = nullptr;             // tree edges per instance (merge rounds)
     nnm_merge *merges_tmp = nullptr;
     float *tile_c = nullptr, *tile_rho = nullptr, *mu_f = nullptr, *blk_c = nullptr, *blk_rho = nullptr;
     // landmark bounds: per row the FP32 squared distance to its nearest landmark (x units),
@@ -212,10 +213,12 @@ uint64_t wait_limit(int64_t ns)
 
 bool is_tensor(const nnm_ctx *c) { return c->prec != NNM_PREC_FP32; }
 
-// Column ranges per row tile: enough CTAs to fill the 152 SMs a few times.
+// Column ranges per row tile: enough CTAs to fill the 152 SMs a few times.  In a batched
+// context a row tile sweeps its own instances' columns (one instance, or several when a
+// short row list mixes instances); the kernels split that range, so the same rule applies
+// (splits beyond a row tile's range are empty and cheap).
 int choose_splits(const nnm_ctx *c, int64_t nslots)
 {
-    if (c->n_inst > 1) return 1;   // each row tile sweeps its own instance only
     if (c->opt.col_split > 0) return c->opt.col_split < kMaxSplits ? c->opt.col_split : kMaxSplits;
     const int64_t row_ctas = (nslots + kRowTile - 1) / kRowTile;
     const int64_t target = is_tensor(c) ? 152 * 4 : 152 * 2 * 4;
@@ -820,6 +823,7 @@ nnm_status ensure_rounds(nnm_ctx *c)
         NNM_TRY(dalloc(c, &c->ebeg, (size_t)c->n_inst));
         NNM_TRY(dalloc(c, &c->eend, (size_t)c->n_inst));
         NNM_TRY(dalloc(c, &c->inst_nm, (size_t)c->n_inst + 1));
+        NNM_TRY(dalloc(c, &c->inst_edges, (size_t)c->n_inst));
         NNM_TRY(dalloc(c, &c->merges_tmp, (size_t)N));
     }
     NNM_TRY(dalloc(c, &c->tile_comp, (size_t)((N + c->tile_w - 1) / c->tile_w)));
@@ -878,6 +882,8 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     st.X = c->X;
     st.d = c->d;
     st.inst_pos = c->inst_pos;
+    st.inst_off = c->inst_off;
+    st.inst_edges = c->n_inst > 1 ? c->inst_edges : nullptr;
     st.metric = c->metric;
     st.row_D = c->row_D;
     st.row_ab = c->row_ab;
@@ -899,6 +905,7 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
         Phase ph(c, &c->stats.ms_rounds);
         NNM_CUDA(c, launch_round_init(st, s));
         NNM_CUDA(c, cudaMemsetAsync(&c->dcount[1], 0, 4 * sizeof(uint32_t), s));
+        if (st.inst_edges) NNM_CUDA(c, cudaMemsetAsync(c->inst_edges, 0, (size_t)c->n_inst * sizeof(uint32_t), s));
     }
     int64_t ncomp = c->N;
     // NNM_TRACE=1 in the environment: one line per merge round on stderr
@@ -968,6 +975,8 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
             NNM_CUDA(c, launch_relabel(st, s));
         }
         ncomp -= nedge;
+        // a batched context is done when every instance is one component
+        if (c->n_inst > 1 && ncomp == c->n_inst) break;
         if (trace) {
             tiles_now(t1);
             fprintf(stderr, "nnm round %d: rescans %u, sweep %.2f ms, rerank %.2f ms, tiles swept %llu skipped %llu, "
@@ -1591,6 +1600,7 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->ebeg);
     dfree(c->eend);
     dfree(c->inst_nm);
+    dfree(c->inst_edges);
     dfree(c->merges_tmp);
     dfree(c->cut_cnt);
     dfree(c->cut_lab);

@@ -353,6 +353,10 @@ struct RoundState {
     int d;
     int metric;
     const uint32_t *inst_pos;      // batched contexts: instance of each position (nullable)
+    const int64_t *inst_off;       // batched: first row of each instance, and N
+    uint32_t *inst_edges;          // batched: tree edges found so far per instance; an
+                                   // instance with rows - 1 of them is one component, so
+                                   // its rows have no outgoing pair and are not rescanned
     unsigned long long *row_D;     // [N] key of the row's best outgoing candidate (D bits)
     unsigned long long *row_ab;    // [N] (min << 32) | max
     uint8_t *row_state;            // 0 none, 1 resolved, 2 unresolved (row_D/row_ab: bound)

@@ -141,7 +141,12 @@ __global__ void k_flag(RoundState st)
     if (i >= st.N) return;
     uint8_t f = 0;
     const uint32_t p = st.row2pos[i];
-    if (st.row_state[i] == 2) {
+    bool done = false;   // the row's instance is one component already
+    if (st.inst_edges) {
+        const uint32_t b = st.inst_pos[i];
+        done = (int64_t)st.inst_edges[b] + 1 == st.inst_off[b + 1] - st.inst_off[b];
+    }
+    if (st.row_state[i] == 2 && !done) {
         const uint32_t c = st.comp[i];
         f = key_less(st.row_D[i], st.row_ab[i], st.best_D[c], st.best_ab[c]);
         if (f) {
@@ -254,6 +259,7 @@ __global__ void k_hook(RoundState st)
     const bool mutual = st.best_D[c2] == st.best_D[c] && st.best_ab[c2] == st.best_ab[c];
     if (mutual && (uint32_t)c < c2) return;   // the smaller id of a mutual pair stays root
     st.parent[c] = c2;
+    if (st.inst_edges) atomicAdd(&st.inst_edges[st.inst_pos[a]], 1u);
     const uint32_t e = atomicAdd(st.n_edges, 1u);
     nnm_edge ed;
     ed.a = a;

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_fp32(const SweepArgs a)
     }
     const int64_t ntile_all = rte - rtb;
     const int64_t tile0 = p_first / kTile - rtb;
-    const int64_t tps = a.cols_per_split / kTile;
+    // tiles per column range: of the whole matrix, or (batched) of this row tile's range
+    const int64_t tps = a.inst_pos ? (ntile_all + a.splits - 1) / a.splits : a.cols_per_split / kTile;
     const int64_t t_begin = (int64_t)split * tps;
     const int64_t t_end = t_begin + tps < ntile_all ? t_begin + tps : ntile_all;
     const int64_t ntiles = t_end > t_begin ? t_end - t_begin : 0;

@@ -32,6 +32,7 @@ constexpr int kPlanQ = 256;       // planned tiles the planner may run ahead of 
 constexpr int kBN = 128;          // columns per B tile
 constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere per block)
 constexpr int kMaxStages = 8;
+constexpr int kMaxKSteps = 6;     // K steps of 16 per tile: kpad <= 96 (split BF16 at d <= 30)
 constexpr int kBandWide = 64;   // band slots per row for one-term BF16 (a wide band)
 constexpr int kStageStride = 36;   // floats per thread in the hit-staging area (16-byte rows, no bank conflicts)
 // Waits for work (stages, accumulators, plan entries, thresholds) give up after the
@@ -200,6 +201,8 @@ struct __align__(8) TcShared {
     int acc_tile[2];             // column tile in each TMEM buffer (-1: end)
     unsigned int ring_mask[kMaxStages];   // epilogue warps that need the tile in each stage
     unsigned int acc_mask[2];             // ... and in each TMEM buffer
+    uint32_t ring_comp[kMaxStages];       // masked sweeps: the tile's component (kInvalid: mixed)
+    uint32_t acc_comp[2];
     float warp_thr[kEpiWarps];   // largest row threshold of each epilogue warp
     float cR[2][32];             // row tile spheres (part 0: the first landmark group of the
     unsigned int rho_bits[2];    // tile's rows, part 1: the rest): centres, radii,
@@ -209,11 +212,12 @@ struct __align__(8) TcShared {
     int npub;                    // epilogue warps that have published a threshold
     int plan_ct[kPlanQ];         // planned column tiles (-1: end), a ring of kPlanQ ...
     unsigned int plan_mask[kPlanQ];   // ... with the epilogue warps that need them
+    uint32_t plan_comp[kPlanQ];       // ... and, in masked sweeps, the tile's component
     int plan_head, plan_tail;
     unsigned int lup_bits[2];    // largest landmark distance bound of each row part    // entries written by the planner / taken by the producer
     unsigned int cmin, cmax;     // smallest and largest component among the tile's rows
 };
-constexpr int kShBytes = 3072;
+constexpr int kShBytes = 4096;
 static_assert(sizeof(TcShared) <= kShBytes, "shared control block");
 
 // Shared-memory stages of the B ring that fit next to the other regions.
@@ -406,6 +410,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             __threadfence_block();
             const int ct = ((volatile int *)sh->plan_ct)[taken % kPlanQ];
             const unsigned int wmask = ((volatile unsigned int *)sh->plan_mask)[taken % kPlanQ];
+            const uint32_t tcomp = ((volatile uint32_t *)sh->plan_comp)[taken % kPlanQ];
             __syncwarp();
             if (lane == 0) ((volatile int *)&sh->plan_tail)[0] = taken + 1;
             const int s = issued % kStages;
@@ -416,6 +421,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             if (lane == 0) {
                 sh->ring_tile[s] = ct;
                 sh->ring_mask[s] = wmask;
+                sh->ring_comp[s] = tcomp;
                 if (ct < 0) {
                     mbar_arrive(&sh->full[s]);
                 } else {
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         int planned = 0;
         bool ok_all = true;
         // append (ct, wmask) to the plan (bounded wait for room; the whole warp polls)
-        auto push = [&](int ct, unsigned int wmask) -> bool {
+        auto push = [&](int ct, unsigned int wmask, uint32_t tcomp) -> bool {
             const uint64_t t0 = global_ns();
             bool ok = true;
             while (planned - ((volatile int *)&sh->plan_tail)[0] >= kPlanQ) {
@@ -469,6 +475,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             if (lane == 0) {
                 ((volatile int *)sh->plan_ct)[planned % kPlanQ] = ct;
                 ((volatile unsigned int *)sh->plan_mask)[planned % kPlanQ] = wmask;
+                ((volatile uint32_t *)sh->plan_comp)[planned % kPlanQ] = tcomp;
                 __threadfence_block();
                 ((volatile int *)&sh->plan_head)[0] = planned + 1;
             }
@@ -518,7 +525,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             // The wait is bounded; on time-out the decisions only get less selective.
             if (!(COLLECT || a.row_B) && nblk > 0) {
                 first = split == 0 ? tile0 : (blk_at(0) * kBlkTiles > rtb ? blk_at(0) * kBlkTiles : rtb);
-                ok_all = push(first, 0xFFu);
+                ok_all = push(first, 0xFFu, a.comp ? a.tile_comp[first] : kInvalid);
             }
             if (ok_all && nblk > 0 && lane == 0) {
                 const uint64_t t0 = global_ns();
@@ -548,9 +555,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 const int t0c = blk_at(u0 + q) * kBlkTiles;
                 const int n = ntile_all - t0c < kBlkTiles ? ntile_all - t0c : kBlkTiles;
                 unsigned int wmask = (lane < n && t0c + lane >= rtb && t0c + lane < rte) ? 0xFFu : 0u;
+                uint32_t tcomp = kInvalid;
                 if (wmask) {
                     const int ct = t0c + lane;
-                    if (ct == first || (rcomp != kInvalid && a.tile_comp[ct] == rcomp)) {
+                    if (a.comp) tcomp = a.tile_comp[ct];
+                    if (ct == first || (rcomp != kInvalid && tcomp == rcomp)) {
                         wmask = 0u;
                     } else if (a.prune) {
                         float lb0 = INFINITY, lb1 = INFINITY;
@@ -570,11 +579,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                     const int e = __ffs(keepm) - 1;
                     keepm &= keepm - 1u;
                     const unsigned int m = __shfl_sync(0xffffffffu, wmask, e);
-                    if (!(ok_all = push(t0c + e, m))) break;
+                    const uint32_t tc = __shfl_sync(0xffffffffu, tcomp, e);
+                    if (!(ok_all = push(t0c + e, m, tc))) break;
                 }
             }
         }
-        if (ok_all) push(-1, 0u);
+        if (ok_all) push(-1, 0u, kInvalid);
         const int taken = planned > 0 ? planned - 1 : 0;   // tiles, without the end marker
         if (lane == 0 && a.st_tiles) {
             atomicAdd(&a.st_tiles[0], (unsigned long long)(range_tiles - taken));
@@ -585,6 +595,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         const uint32_t lbo = 128, sbo = (uint32_t)(kpad / 8) * 128;
         const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB);
         const int ksteps = kpad / 16;
+        const uint64_t adesc0[2] = {smem_desc(aaddr, lbo, sbo), smem_desc(aaddr + 16u * sbo, lbo, sbo)};
+        const uint64_t bdesc0 = smem_desc(baddr, lbo, sbo);
         int done = 0;
         for (int q = 0;; ++q) {
             const int s = q % kStages, b = q & 1;
@@ -603,15 +615,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             if (lane == 0) {
                 ((volatile int *)sh->acc_tile)[b] = tile;
                 ((volatile unsigned int *)sh->acc_mask)[b] = ((volatile unsigned int *)sh->ring_mask)[s];
+                ((volatile uint32_t *)sh->acc_comp)[b] = ((volatile uint32_t *)sh->ring_comp)[s];
                 if (tile >= 0) {
+                    // descriptors: the start-address field (bits 0-13, address >> 4) of the
+                    // stage's base plus 16 per K step of 16 (256 bytes); shared addresses stay
+                    // below 2^18, so the field never carries into the next one
+                    const uint64_t bd0 = bdesc0 + (uint64_t)(((uint32_t)s * b_bytes) >> 4);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         const uint32_t d_tmem = tmem + (uint32_t)((b * 2 + h) * kBN);
-                        for (int kk = 0; kk < ksteps; ++kk) {
-                            uint64_t ad = smem_desc(aaddr + (uint32_t)h * 16u * sbo + (uint32_t)kk * 256u, lbo, sbo);
-                            uint64_t bd = smem_desc(baddr + (uint32_t)s * b_bytes + (uint32_t)kk * 256u, lbo, sbo);
-                            mma_f16(d_tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
-                        }
+                        const uint64_t ad0 = adesc0[h];
+#pragma unroll
+                        for (int kk = 0; kk < kMaxKSteps; ++kk)
+                            if (kk < ksteps) mma_f16(d_tmem, ad0 + 16u * kk, bd0 + 16u * kk, idesc, kk > 0 ? 1u : 0u);
                     }
                     mma_commit(&sh->empty[s]);
                     mma_commit(&sh->tfull[b]);
@@ -652,11 +668,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             if (B < INFINITY) sel.bound(sel_threshold(a.sc, rc, __double2float_ru(B / a.m.inv_scale2)));
         }
         if (!COLLECT && a.splits > 1 && valid) sel.bound(shared_thr_exchange(&a.slot_thr[slot0 + myrow_slot], INFINITY));
+        // the warp's largest threshold: thresholds are non-negative floats or -inf, whose
+        // bit patterns order as signed integers, so one integer max reduction gives it
         auto publish = [&]() {
-            float wt = COLLECT ? cthr : sel.thr;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wt = fmaxf(wt, __shfl_xor_sync(0xffffffffu, wt, o));
-            if (lane == 0) ((volatile float *)sh->warp_thr)[warp] = wt;
+            const int wt = __reduce_max_sync(0xffffffffu, __float_as_int(COLLECT ? cthr : sel.thr));
+            if (lane == 0) ((volatile float *)sh->warp_thr)[warp] = __int_as_float(wt);
         };
         bool published = false;
         if (a.prune && (COLLECT || a.row_B)) {
@@ -721,28 +737,28 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             // the tile number comes from lane 0 so that the whole warp decides alike
             tc_fence_after();
-            int tile = 0;
-            unsigned int wmask = 0u;
+            // tile number (-1: end) and this warp's bit of the mask in one word
+            int tw = 0;
+            uint32_t tcm = kInvalid;
             if (lane == 0) {
-                tile = ((volatile int *)sh->acc_tile)[b];
-                wmask = ((volatile unsigned int *)sh->acc_mask)[b];
+                const int tl = ((volatile int *)sh->acc_tile)[b];
+                const unsigned int m = ((volatile unsigned int *)sh->acc_mask)[b];
+                tw = tl < 0 ? -1 : (tl << 1) | (int)((m >> warp) & 1u);
+                tcm = ((volatile uint32_t *)sh->acc_comp)[b];
             }
-            tile = __shfl_sync(0xffffffffu, tile, 0);
-            wmask = __shfl_sync(0xffffffffu, wmask, 0);
-            if (tile < 0) break;
+            tw = __shfl_sync(0xffffffffu, tw, 0);
+            if (tw < 0) break;
+            const int tile = tw >> 1;
             const int64_t col0 = (int64_t)tile * kBN;
-            if (!((wmask >> warp) & 1u)) {
+            if (!(tw & 1)) {
                 // no row of this warp can have a candidate in the tile: release the buffer
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sh->tempty[b]);
                 continue;
             }
-            if (a.comp) {
-                uint32_t tc = 0;
-                if (lane == 0) tc = a.tile_comp[tile];
-                tcomp = __shfl_sync(0xffffffffu, tc, 0);
-            }
+            // the tile's component travelled with it through the plan and the ring
+            if (a.comp) tcomp = __shfl_sync(0xffffffffu, tcm, 0);
             // a row of the tile's own component has nothing eligible in it
             const bool own = a.comp && tcomp != kInvalid && tcomp == mycomp;
             const uint32_t taddr = lane_base + (uint32_t)((b * 2 + half) * kBN);
@@ -819,7 +835,7 @@ template <int CB>
 static cudaError_t go_tc_band(const SweepArgs &a, bool collect, dim3 grid, cudaStream_t s)
 {
     const size_t smem = sweep_tc_smem_bytes(a.kpad, CB);
-    if (tc_stages(a.kpad, CB) < 2) return cudaErrorInvalidValue;
+    if (tc_stages(a.kpad, CB) < 2 || a.kpad > 16 * kMaxKSteps || a.kpad % 16) return cudaErrorInvalidValue;
     if (collect) return go_tc<1, CB, true>(a, grid, smem, s);
     if (a.kc <= 1) return go_tc<1, CB, false>(a, grid, smem, s);
     if (a.kc <= 2) return go_tc<2, CB, false>(a, grid, smem, s);
