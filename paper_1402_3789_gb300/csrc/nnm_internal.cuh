@@ -21,6 +21,23 @@ constexpr int kMaxK = 16;         // largest k of nnm_nearest / cache width
 constexpr int kRowTile = 256;     // rows per sweep CTA (both candidate paths)
 constexpr int kMaxSplits = 32;    // column ranges per row tile
 constexpr uint64_t kMaxKey = 0xFFFFFFFFFFFFFFFFull;
+// Kernels whose dynamic shared memory depends on the launch set their limit to the
+// largest the device allows them (its opt-in maximum less the kernel's static shared
+// memory), one value per kernel: the limit is a per-function attribute, and host threads
+// launching on different streams must not lower it below each other's requests (the
+// request at launch still decides the occupancy).
+template <typename Kernel>
+inline cudaError_t set_max_dynamic_smem(Kernel *k)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
 
 // State of a row's neighbour cache after a scan for its k nearest eligible columns:
 constexpr uint8_t kCacheFull = 0;      // k found: every other eligible column has a larger key
@@ -496,6 +513,27 @@ cudaError_t launch_lit_exact(const LitArgs &a, cudaStream_t s);
 cudaError_t launch_lit_flatten(const LitArgs &a, cudaStream_t s);
 cudaError_t launch_lit_init(const LitArgs &a, double t0, cudaStream_t s);
 cudaError_t launch_lit_reach(const LitArgs &a, const nnm_merge *merges, int64_t n1, cudaStream_t s);
+
+// KL2 / KL3 without KL4, one instance (dendro.cu): safe edges joined in parallel, the
+// walk only over the others.  cand: the admissible edges as nnm_merge records in key
+// order with their unrestricted new sizes, w: the two unrestricted endpoint sizes.
+struct FastWalkArgs {
+    int64_t N, M;
+    int64_t kl2, kl3;
+    nnm_merge *cand;           // [M] admissible edges (key order); new sizes fixed here
+    const uint32_t *w;         // [2M] unrestricted sizes of both endpoints' clusters before each edge
+    uint8_t *dec;              // [M] 1: joined
+    uint8_t *unsafe;           // [M] 1: the walk decides it
+    uint32_t *pos;             // [M] positions (compaction output)
+    nnm_edge *unsafe_edges;    // [M] the unsafe edges in key order (the walk's input)
+    nnm_merge *walk_out;       // [M] the walk's joins (key order)
+    uint32_t *uf_parent, *uf_size;   // [N]
+    nnm_merge *merges;         // [N-1] out
+    int *err_flag;
+};
+// step 0 mark, 1 join safe edges and size the clusters, 2 gather n unsafe edges (pos),
+// 3 place n accepted unsafe joins, 4 emit n joins (pos), 5 final union-find of n joins
+cudaError_t launch_fast_walk_steps(const FastWalkArgs &f, int step, int64_t n, cudaStream_t s);
 
 struct LabelArgs {
     int64_t N;

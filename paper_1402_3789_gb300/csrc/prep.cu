@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kMaxLandmarks) k_landmark_chain(const float *_
 cudaError_t launch_landmark_chain(const float *X, int64_t N, int d, int64_t L, uint32_t *rank, cudaStream_t s)
 {
     const size_t smem = (size_t)L * d * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_landmark_chain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_dynamic_smem(k_landmark_chain);
     if (e != cudaSuccess) return e;
     k_landmark_chain<<<1, kMaxLandmarks, smem, s>>>(X, N, d, (int)L, rank);
     count_launches(1);

@@ -336,7 +336,7 @@ cudaError_t launch_finalize(const FinalizeArgs &a, cudaStream_t s)
     if (a.nslots <= 0) return cudaSuccess;
     const size_t smem = (size_t)kFinWarps * a.splits * kListC * (8 + 4 + 4) +   // <= 160 KB
                         (size_t)kFinWarps * ed_scratch_bytes(a.d);             // <= 35 KB
-    cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_dynamic_smem(k_finalize);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)((a.nslots + kFinWarps - 1) / kFinWarps);
     k_finalize<<<blocks, kFinWarps * 32, smem, s>>>(a);

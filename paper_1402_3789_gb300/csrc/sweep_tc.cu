@@ -823,8 +823,7 @@ size_t sweep_tc_smem_bytes(int kpad, int band)
 template <int KC, int CB, bool COLL>
 static cudaError_t go_tc(const SweepArgs &a, dim3 grid, size_t smem, cudaStream_t s)
 {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_sweep_tc<KC, CB, COLL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_max_dynamic_smem(k_sweep_tc<KC, CB, COLL>);
     if (e != cudaSuccess) return e;
     k_sweep_tc<KC, CB, COLL><<<grid, kThreadsTc, smem, s>>>(a);
     count_launches(1);
