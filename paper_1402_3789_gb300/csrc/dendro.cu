@@ -212,6 +212,127 @@ __global__ void k_uf_merges(const CutArgs a, int64_t M)
 
 inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
+// ---------------------------------------------------------------------------------
+// KL2 / KL3 without KL4 (one instance): most decisions without the walk.  With the
+// unrestricted process's cluster sizes s_a, s_b just before each admissible edge (the
+// cut's levels above, KL1 left out), an edge with s_a + s_b <= KL3 and s_a, s_b <= KL2 is
+// joined whatever the restricted sizes are (they are no larger), and so is every edge
+// below it in the merge tree (their sizes are smaller): these "safe" edges are joined,
+// with new size s_a + s_b.  Everything above an unsafe edge is unsafe, so an unsafe
+// edge's clusters are made only of edges below it: the union-find with every safe edge
+// applied serves all unsafe edges, which the walk then decides in key order.  KL1 only
+// cuts the accepted sequence after N - KL1 joins.
+// ---------------------------------------------------------------------------------
+__global__ void k_fw_mark(const FastWalkArgs f)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= f.M) return;
+    const int64_t sa = f.w[2 * j], sb = f.w[2 * j + 1];
+    const bool safe = (f.kl3 <= 0 || sa + sb <= f.kl3) && (f.kl2 <= 0 || (sa <= f.kl2 && sb <= f.kl2));
+    f.dec[j] = safe ? 1 : 0;
+    f.unsafe[j] = safe ? 0 : 1;
+}
+
+__global__ void k_fw_union_safe(const FastWalkArgs f)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= f.M || !f.dec[j]) return;
+    if (!cunion(f.uf_parent, f.cand[j].a, f.cand[j].b)) atomicExch(f.err_flag, 1);
+}
+
+__global__ void k_fw_sizes(const FastWalkArgs f)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f.N) return;
+    atomicAdd(f.uf_size + cfind(f.uf_parent, (uint32_t)i), 1u);
+}
+
+__global__ void k_fw_gather_unsafe(const FastWalkArgs f, int64_t n)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const nnm_merge m = f.cand[f.pos[t]];
+    nnm_edge e;
+    e.a = m.a;
+    e.b = m.b;
+    e.D = m.D;
+    f.unsafe_edges[t] = e;
+}
+
+// an accepted unsafe edge back at its place among the admissible edges (keys are unique)
+__global__ void k_fw_place(const FastWalkArgs f, int64_t n)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const nnm_merge m = f.walk_out[t];
+    const long long dm = __double_as_longlong(m.D);
+    int64_t lo = 0, hi = f.M;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const nnm_merge c = f.cand[mid];
+        const long long dc = __double_as_longlong(c.D);
+        const bool less = dc < dm || (dc == dm && (c.a < m.a || (c.a == m.a && c.b < m.b)));
+        if (less) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < f.M && f.cand[lo].a == m.a && f.cand[lo].b == m.b) {
+        f.dec[lo] = 1;
+        f.cand[lo].new_size = m.new_size;
+    } else {
+        atomicExch(f.err_flag, 1);
+    }
+}
+
+__global__ void k_fw_emit(const FastWalkArgs f, int64_t n)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) f.merges[k] = f.cand[f.pos[k]];
+}
+
+}  // namespace
+
+cudaError_t launch_fast_walk_steps(const FastWalkArgs &f, int step, int64_t n, cudaStream_t s)
+{
+    switch (step) {
+    case 0:
+        if (f.M > 0) k_fw_mark<<<blocks_for(f.M), kThreads, 0, s>>>(f);
+        break;
+    case 1:
+        k_uf_init<<<blocks_for(f.N), kThreads, 0, s>>>(f.uf_parent, f.N);
+        if (f.M > 0) k_fw_union_safe<<<blocks_for(f.M), kThreads, 0, s>>>(f);
+        if (cudaMemsetAsync(f.uf_size, 0, (size_t)f.N * sizeof(uint32_t), s) != cudaSuccess) return cudaGetLastError();
+        k_fw_sizes<<<blocks_for(f.N), kThreads, 0, s>>>(f);
+        count_launches(1);
+        break;
+    case 2:
+        if (n > 0) k_fw_gather_unsafe<<<blocks_for(n), kThreads, 0, s>>>(f, n);
+        break;
+    case 3:
+        if (n > 0) k_fw_place<<<blocks_for(n), kThreads, 0, s>>>(f, n);
+        break;
+    case 4:
+        if (n > 0) k_fw_emit<<<blocks_for(n), kThreads, 0, s>>>(f, n);
+        break;
+    case 5:
+        // the final partition: the emitted joins only (KL1 may have cut the sequence)
+        k_uf_init<<<blocks_for(f.N), kThreads, 0, s>>>(f.uf_parent, f.N);
+        if (n > 0) {
+            CutArgs a{};
+            a.merges = f.merges;
+            a.uf_parent = f.uf_parent;
+            a.err_flag = f.err_flag;
+            k_uf_merges<<<blocks_for(n), kThreads, 0, s>>>(a, n);
+            count_launches(1);
+        }
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+namespace {
 }  // namespace
 
 int64_t cut_hash_slots(int64_t m)

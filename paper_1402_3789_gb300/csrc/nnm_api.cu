@@ -112,6 +112,13 @@ struct nnm_ctx {
     uint32_t *cut_lab = nullptr, *cut_w = nullptr, *cut_slot = nullptr;
     uint32_t *cut_hpar = nullptr, *cut_hw = nullptr, *cut_hsum = nullptr, *cut_hlab = nullptr;
     int64_t cut_cap = 0, cut_H = 0;
+    // KL2 / KL3 without KL4: safe edges in parallel, the walk only over the others
+    nnm_merge *fw_cand = nullptr, *fw_walk = nullptr;
+    uint8_t *fw_dec = nullptr, *fw_unsafe = nullptr;
+    uint32_t *fw_pos = nullptr, *fw_blk = nullptr;
+    nnm_edge *fw_edges = nullptr;
+    unsigned long long *fw_cnt = nullptr;   // [0] walk joins [1] joined count (walk state) [2] stop flag
+    int64_t fw_cap = 0;
     // small device block: counters and statistics
     uint32_t *dcount = nullptr;             // [0] ovf, [1..3] round counters, [4] n_edges
     unsigned long long *dstat = nullptr;    // [0] max_abs [1] max_rel [2] pairs [3] max_cand [4] n_merges [5] K [6] maxbits..
@@ -309,6 +316,22 @@ nnm_status ensure_cut(nnm_ctx *c, int64_t m)
     NNM_TRY(dalloc(c, &c->cut_hlab, (size_t)H));
     c->cut_cap = m;
     c->cut_H = H;
+    return NNM_OK;
+}
+
+nnm_status ensure_fast(nnm_ctx *c)
+{
+    if (c->fw_cap >= c->N) return NNM_OK;
+    const size_t n = (size_t)c->N;
+    NNM_TRY(dalloc(c, &c->fw_cand, n));
+    NNM_TRY(dalloc(c, &c->fw_walk, n));
+    NNM_TRY(dalloc(c, &c->fw_dec, n));
+    NNM_TRY(dalloc(c, &c->fw_unsafe, n));
+    NNM_TRY(dalloc(c, &c->fw_pos, n));
+    NNM_TRY(dalloc(c, &c->fw_blk, (size_t)compact_blocks(c->N)));
+    NNM_TRY(dalloc(c, &c->fw_edges, n));
+    NNM_TRY(dalloc(c, &c->fw_cnt, 4));
+    c->fw_cap = c->N;
     return NNM_OK;
 }
 
@@ -1007,6 +1030,103 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
     return NNM_OK;
 }
 
+// KL2 / KL3 without KL4 on one instance (dendro.cu has the argument): the unrestricted
+// endpoint sizes of every admissible edge from the cut's levels, the safe edges joined in
+// parallel, the walk over the unsafe ones only, then the joins in key order, cut after
+// N - KL1 of them.  Leaves the final partition in uf_parent and the count in dstat[4].
+nnm_status restrict_fast(nnm_ctx *c, const nnm_restrictions &r, double cap2, nnm_merge *merges_dev)
+{
+    cudaStream_t s = c->stream;
+    const int64_t N = c->N;
+    NNM_TRY(ensure_cut(c, c->n_tree));
+    NNM_TRY(ensure_fast(c));
+    CutArgs ca{};
+    ca.edges = c->tree;
+    ca.m = c->n_tree;
+    ca.N = N;
+    ca.cap2 = cap2;
+    ca.kl1 = 0;
+    ca.metric = c->metric;
+    ca.n_inst = 1;
+    ca.merges = c->fw_cand;
+    ca.n_merges = &c->dstat[4];
+    ca.uf_parent = c->uf_parent;
+    ca.err_flag = &c->derr[3];
+    ca.cnt = c->cut_cnt;
+    ca.lab = c->cut_lab;
+    ca.w = c->cut_w;
+    ca.slot = c->cut_slot;
+    ca.hkey = c->cut_hkey;
+    ca.hpar = c->cut_hpar;
+    ca.hw = c->cut_hw;
+    ca.hsum = c->cut_hsum;
+    ca.hlab = c->cut_hlab;
+    ca.H = c->cut_H;
+    int64_t M = 0;
+    NNM_CUDA(c, launch_restrict_cut(ca, &M, s));
+    FastWalkArgs f{};
+    f.N = N;
+    f.M = M;
+    f.kl2 = r.kl2_max_pre_size;
+    f.kl3 = r.kl3_max_size;
+    f.cand = c->fw_cand;
+    f.w = c->cut_w;
+    f.dec = c->fw_dec;
+    f.unsafe = c->fw_unsafe;
+    f.pos = c->fw_pos;
+    f.unsafe_edges = c->fw_edges;
+    f.walk_out = c->fw_walk;
+    f.uf_parent = c->uf_parent;
+    f.uf_size = c->uf_size;
+    f.merges = merges_dev;
+    f.err_flag = &c->derr[3];
+    NNM_CUDA(c, launch_fast_walk_steps(f, 0, 0, s));
+    NNM_CUDA(c, launch_fast_walk_steps(f, 1, 0, s));
+    uint32_t n_unsafe = 0;
+    NNM_CUDA(c, launch_compact(c->fw_unsafe, M, nullptr, nullptr, c->fw_blk, c->fw_pos, nullptr, &c->dcount[6], s));
+    NNM_TRY(read_dev(c, &n_unsafe, &c->dcount[6]));
+    if (n_unsafe > 0) {
+        NNM_CUDA(c, launch_fast_walk_steps(f, 2, n_unsafe, s));
+        NNM_CUDA(c, cudaMemsetAsync(c->fw_cnt, 0, 4 * sizeof(unsigned long long), s));
+        RestrictArgs ra{};
+        ra.edges = c->fw_edges;
+        ra.m = n_unsafe;
+        ra.N = N;
+        ra.cap2 = cap2;
+        ra.kl2 = r.kl2_max_pre_size;
+        ra.kl3 = r.kl3_max_size;
+        ra.uf_parent = c->uf_parent;
+        ra.uf_size = c->uf_size;
+        ra.merges = c->fw_walk;
+        ra.n_merges = &c->fw_cnt[0];
+        ra.err_flag = &c->derr[3];
+        ra.n_inst = 1;
+        ra.metric = c->metric;
+        ra.persist = 1;
+        ra.lit_phase = 2;
+        ra.joined_io = reinterpret_cast<long long *>(&c->fw_cnt[1]);
+        ra.stop_io = reinterpret_cast<int *>(&c->fw_cnt[2]);
+        NNM_CUDA(c, launch_restrict(ra, s));
+        unsigned long long n_acc = 0;
+        NNM_TRY(read_dev(c, &n_acc, &c->fw_cnt[0]));
+        NNM_CUDA(c, launch_fast_walk_steps(f, 3, (int64_t)n_acc, s));
+    }
+    uint32_t n_dec = 0;
+    NNM_CUDA(c, launch_compact(c->fw_dec, M, nullptr, nullptr, c->fw_blk, c->fw_pos, nullptr, &c->dcount[6], s));
+    NNM_TRY(read_dev(c, &n_dec, &c->dcount[6]));
+    int64_t n_out = n_dec;
+    if (r.kl1_stop_clusters > 0) {
+        const int64_t room = N > r.kl1_stop_clusters ? N - r.kl1_stop_clusters : 0;
+        if (n_out > room) n_out = room;
+    }
+    NNM_CUDA(c, launch_fast_walk_steps(f, 4, n_out, s));
+    NNM_CUDA(c, launch_fast_walk_steps(f, 5, n_out, s));
+    const unsigned long long nm = (unsigned long long)n_out;
+    NNM_CUDA(c, cudaMemcpyAsync(&c->dstat[4], &nm, sizeof nm, cudaMemcpyHostToDevice, s));
+    NNM_CUDA(c, cudaStreamSynchronize(s));
+    return NNM_OK;
+}
+
 constexpr int64_t kLiteralMaxRows = 262144;
 
 // Device buffers of one call, freed when it returns.
@@ -1450,6 +1570,10 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
             ca.hlab = c->cut_hlab;
             ca.H = c->cut_H;
             NNM_CUDA(c, launch_restrict_cut(ca, &n_cut, c->stream));
+        } else if (r.kl4_min_size == 0 && c->n_inst == 1) {
+            // KL2 / KL3 only: safe edges in parallel, the walk over the others
+            Phase ph(c, &c->stats.ms_restrict);
+            NNM_TRY(restrict_fast(c, r, cap2, merges_dev));
         } else {
             Phase ph(c, &c->stats.ms_restrict);
             RestrictArgs ra{};
@@ -1611,6 +1735,14 @@ void nnm_destroy(nnm_ctx *c)
     dfree(c->cut_hw);
     dfree(c->cut_hsum);
     dfree(c->cut_hlab);
+    dfree(c->fw_cand);
+    dfree(c->fw_walk);
+    dfree(c->fw_dec);
+    dfree(c->fw_unsafe);
+    dfree(c->fw_pos);
+    dfree(c->fw_blk);
+    dfree(c->fw_edges);
+    dfree(c->fw_cnt);
     dfree(c->blk_c);
     dfree(c->blk_rho);
     dfree(c->mu_f);

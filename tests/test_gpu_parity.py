@@ -452,3 +452,42 @@ def test_other_metrics_need_the_fp32_path(nnm):
     for p in ("bf16", "fp16", "bf16x3"):
         with pytest.raises(nnm.NNMError):
             nnm.nnm_create(X, precision=p, metric="manhattan")
+
+
+# ----------------------------------------------------------------------------------
+# KL2 / KL3 without KL4: safe edges joined in parallel, the walk over the others only
+# ----------------------------------------------------------------------------------
+
+def _chain(n):
+    """Rows on a line with growing gaps: one long chain in the merge tree (every join
+    adds one row to the big cluster), the case where most edges are unsafe."""
+    x = np.cumsum(np.linspace(0.01, 1.0, n)).astype(np.float32)
+    return np.stack([x, np.zeros_like(x)], axis=1)
+
+
+@pytest.mark.parametrize("restr", [
+    {"kl3_max_size": 700}, {"kl2_max_pre_size": 300}, {"kl3_max_size": 900, "kl2_max_pre_size": 250},
+    {"kl3_max_size": 500, "kl1_stop_clusters": 30}, {"kl3_max_size": 800, "max_join_dist": 1.3},
+    {"kl2_max_pre_size": 1, "kl3_max_size": 2}, {"kl3_max_size": 100000},
+], ids=["kl3", "kl2", "kl2kl3", "kl3kl1", "kl3cap", "tiny", "kl3large"])
+@pytest.mark.parametrize("data", ["mixture", "chain", "ties"])
+def test_size_gates_without_kl4_match_the_oracle(nnm, orc, restr, data):
+    if data == "mixture":
+        from paper_1402_3789_gb300.inputs import make
+        X = make("nnm_n4096_d8", n=30000, seed=77)
+    elif data == "chain":
+        X = _chain(5000)
+    else:
+        rng = np.random.default_rng(3)
+        X = (np.round(rng.uniform(0, 6, size=(8000, 3)) * 4) / 4).astype(np.float32)
+    N = X.shape[0]
+    ctx = nnm.nnm_create(dev(X), precision="fp32")
+    try:
+        res = nnm.nnm_cluster(ctx, restr)
+        tree = nnm.nnm_get_tree(ctx)
+    finally:
+        nnm.nnm_destroy(ctx)
+    om = orc.restrict_tree(tree, N, restr)
+    olab, oK = orc.labels(om, N)
+    assert np.array_equal(res.merges(), om)
+    assert np.array_equal(res.labels.cpu().numpy(), olab) and res.n_clusters == oK
