@@ -499,14 +499,14 @@ def run_batched(args, world, rank):
     # the autotuned form: one batched context per (N, d) bucket with the tuned setting of
     # that bucket (paper_1402_3789_gb300/tuning/gb300_batched.json), buckets concurrently
     from paper_1402_3789_gb300 import autotune
-    table = autotune.load_table()
+    tuning = autotune.load_tuning()
     tuned_ms = None
-    if table:
-        autotune.cluster_batched(Xs, {}, table)
+    if tuning:
+        autotune.run(Xs, {}, tuning)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            autotune.cluster_batched(Xs, {}, table)
+            autotune.run(Xs, {}, tuning)
         torch.cuda.synchronize()
         tuned_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, world)
     line = {"metric": "G pair-distances/s, 512 independent dendrograms in one batched context",
@@ -525,10 +525,12 @@ def run_batched(args, world, rank):
             "one_context_per_instance_ms": loop_ms, "clocks": clocks}
     if tuned_ms is not None:
         line["autotuned"] = {"ms_per_step": tuned_ms, "value": world * pairs / (tuned_ms / 1e3) / 1e9,
-                             "unit": UNIT, "buckets": len(table),
-                             "note": "one batched context per (N, d) bucket with its tuned precision and cache "
-                                     "width, buckets concurrently on separate streams; wall-clock per pass "
-                                     "including the copies of merges and labels to the host"}
+                             "unit": UNIT, "mode": tuning.get("mode"), "global": tuning.get("global"),
+                             "buckets": len(tuning.get("table", {})),
+                             "note": "the tuned run (paper_1402_3789_gb300/tuning/gb300_batched.json): one "
+                                     "batched context with the tuned setting, or one per (N, d) bucket "
+                                     "concurrently, whichever the tuning measured faster; wall-clock per "
+                                     "pass, results on the device"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
