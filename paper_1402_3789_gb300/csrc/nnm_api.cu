@@ -54,6 +54,7 @@ struct nnm_ctx {
     // batched contexts: independent instances of contiguous rows (n_inst == 1: none)
     int64_t n_inst = 1;
     int64_t min_inst_rows = 0;
+    int64_t max_inst_rows = 0;
     int64_t *inst_off = nullptr;   // device [n_inst + 1]; positions = rows of each instance
     uint32_t *inst_pos = nullptr;  // device [N]: instance of each position (and row)
     int64_t *ebeg = nullptr, *eend = nullptr;   // edge range of each instance in the tree
@@ -959,6 +960,7 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
         }
         NNM_TRY(read_dev(c, &nres, &c->dcount[1]));
         std::vector<double> trace_B;
+        std::vector<uint32_t> trace_rows;
         if (trace && nres > 0) {
             // rescan bounds of the flagged rows
             std::vector<uint32_t> lst(nres);
@@ -967,6 +969,7 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
             cudaMemcpyAsync(rb.data(), c->row_B, c->N * sizeof(double), cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
             for (uint32_t q = 0; q < nres; ++q) trace_B.push_back(rb[lst[q]]);
+            trace_rows = lst;
         }
         if (nres > 0) {
             c->stats.rows_rescanned += nres;
@@ -976,6 +979,34 @@ nnm_status build_tree(nnm_ctx *c, double cap2)
             Phase ph(c, &c->stats.ms_rounds);
             NNM_CUDA(c, launch_resolve(st, c->list, nres, s));
             NNM_CUDA(c, launch_component_min(st, s));
+        }
+        if (trace && nres > 0) {
+            // how far the rescan bound (without the overscan) was from the minimum the
+            // component's rescan found: per component, sqrt(bound / minimum)
+            std::vector<uint32_t> comp(c->N);
+            std::vector<unsigned long long> best(c->N);
+            cudaMemcpyAsync(comp.data(), c->comp, c->N * sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(best.data(), c->best_D, c->N * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            std::vector<double> ratio;
+            std::vector<uint8_t> seen(c->N, 0);
+            for (size_t q = 0; q < trace_rows.size(); ++q) {
+                const uint32_t cc = comp[trace_rows[q]];
+                if (seen[cc] || best[cc] == kMaxKey) continue;
+                seen[cc] = 1;
+                double bd;
+                memcpy(&bd, &best[cc], 8);
+                const double B = trace_B[q] / st.overscan;
+                if (B < INFINITY && bd > 0.0) ratio.push_back(sqrt(B / bd));
+            }
+            if (!ratio.empty()) {
+                std::sort(ratio.begin(), ratio.end());
+                const size_t m = ratio.size();
+                size_t over = 0;
+                for (double r : ratio) over += r > 1.1;
+                fprintf(stderr, "    bound / found minimum (distance ratio) over %zu components: 10/50/90%%: %.3f %.3f %.3f, "
+                                "above 1.1: %zu\n", m, ratio[m / 10], ratio[m / 2], ratio[(9 * m) / 10], over);
+            }
         }
         uint32_t nedge = 0;
         {
@@ -1422,12 +1453,14 @@ static nnm_status create_impl(const float *X_dev, int64_t N, int32_t d, const in
     if (options && (options->cache_k < 0 || options->cache_k > 16 || options->col_split < 0 ||
                     options->wait_limit_ns < 0))
         return NNM_EINVAL;
-    int64_t min_rows = N;
+    int64_t min_rows = N, max_rows = N;
     if (offsets) {
         if (n_inst < 1 || n_inst > 65535 || offsets[0] != 0 || offsets[n_inst] != N) return NNM_EINVAL;
+        max_rows = 0;
         for (int64_t b = 0; b < n_inst; ++b) {
             if (offsets[b + 1] <= offsets[b]) return NNM_EINVAL;
             if (offsets[b + 1] - offsets[b] < min_rows) min_rows = offsets[b + 1] - offsets[b];
+            if (offsets[b + 1] - offsets[b] > max_rows) max_rows = offsets[b + 1] - offsets[b];
         }
     }
     nnm_ctx *c = new nnm_ctx();
@@ -1444,6 +1477,7 @@ static nnm_status create_impl(const float *X_dev, int64_t N, int32_t d, const in
     if (c->kc > N - 1) c->kc = N > 1 ? (int)(N - 1) : 1;
     c->kr = c->kc;
     c->min_inst_rows = min_rows;
+    c->max_inst_rows = max_rows;
     cudaGetDevice(&c->device);
     cudaEventCreate(&c->ev0);
     cudaEventCreate(&c->ev1);
@@ -1538,8 +1572,12 @@ nnm_status nnm_cluster(nnm_ctx *c, const nnm_restrictions *restr, nnm_merge *mer
         Phase total(c, &c->stats.ms_total);
         NNM_TRY(build_tree(c, c->opt.freeze_at_cap ? cap2 : INFINITY));
         const bool size_gates = r.kl2_max_pre_size > 0 || r.kl3_max_size > 0 || r.kl4_min_size > 0;
+        // Many instances, none large: the per-instance walks (one CTA each, in parallel,
+        // about 0.3 us per edge of the largest instance) beat the cut's levels over every
+        // edge of the batch (about 9 ns per edge once its hash table leaves L2).
+        const bool walk_instances = c->n_inst > 1 && c->max_inst_rows * 32 < c->N;
         int64_t n_cut = 0;
-        if (!size_gates) {
+        if (!size_gates && !walk_instances) {
             // only the cap and KL1: a parallel cut, new sizes by halving rank ranges
             Phase ph(c, &c->stats.ms_restrict);
             NNM_TRY(ensure_cut(c, c->n_tree));

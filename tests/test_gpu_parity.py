@@ -491,3 +491,33 @@ def test_size_gates_without_kl4_match_the_oracle(nnm, orc, restr, data):
     olab, oK = orc.labels(om, N)
     assert np.array_equal(res.merges(), om)
     assert np.array_equal(res.labels.cpu().numpy(), olab) and res.n_clusters == oK
+
+
+@pytest.mark.parametrize("restr", [{}, {"max_join_dist": 1.0}, {"kl1_stop_clusters": 5},
+                                   {"max_join_dist": 1.4, "kl1_stop_clusters": 9}], ids=["none", "cap", "kl1", "capkl1"])
+def test_batched_many_small_instances_walk_each_instance(nnm, orc, restr):
+    """64 instances, the largest under 1/32 of the rows: the restriction step walks each
+    instance in its own CTA instead of cutting the whole batch."""
+    from paper_1402_3789_gb300.inputs import batched_instances
+    inst = batched_instances(count=64, seed=29, n_lo=150, n_hi=480, d_lo=3, d_hi=20)
+    assert max(x.shape[0] for x in inst) * 32 < sum(x.shape[0] for x in inst)
+    ctx = nnm.nnm_create_batched([dev(x) for x in inst], precision="bf16x3")
+    try:
+        off = ctx.offsets
+        res = nnm.nnm_cluster(ctx, restr)
+        merges = res.merges()
+        lab = res.labels.cpu().numpy()
+    finally:
+        nnm.nnm_destroy(ctx)
+    inst_of = np.searchsorted(np.array(off), np.arange(off[-1]), side="right") - 1
+    k_before = 0
+    for b, X in enumerate(inst):
+        lo = off[b]
+        _, om, olab, oK = orc.cluster(X, restr)
+        m = merges[inst_of[merges["a"]] == b].copy()
+        m["a"] -= lo
+        m["b"] -= lo
+        assert np.array_equal(m, om), b
+        assert np.array_equal(lab[lo:off[b + 1]], olab + k_before), b
+        k_before += oK
+    assert res.n_clusters == k_before
