@@ -8,12 +8,14 @@
 // values, then the rare slow path) -- distances and minimum selection fused, the
 // paper's second and third parallel items.
 //
-// CTA = 256 rows (two M=128 MMAs sharing each B tile) x one column range, 320 threads:
+// CTA = 256 rows (two M=128 MMAs sharing each B tile) x one column range, 384 threads:
 //   warps 0-7  epilogue, one row per thread (TMEM lane quadrant = warp % 4, half = warp / 4)
 //   warp 8     MMA issuer (one elected thread); also allocates / frees TMEM
 //   warp 9     producer: 1-D bulk copies (cp.async.bulk) of 128-column B tiles into an
 //              S-stage shared-memory ring; the operand is stored in HBM already in the
 //              core-matrix layout the MMA reads, so each tile is one contiguous copy.
+//   warps 10-11 planners: bound tests that decide the column tiles, each for half of the
+//              column blocks, ahead of the producer through shared-memory queues.
 // TMEM: 512 columns = 2 accumulator buffers x 2 row halves x 128 columns (fp32).
 // Every wait is bounded (global timer); on time-out the CTA raises the error flag,
 // drains its own copies and MMAs with bounded waits, frees TMEM and exits.
@@ -24,11 +26,13 @@ namespace nnm {
 namespace {
 
 constexpr int kEpiWarps = 8;
-constexpr int kThreadsTc = (kEpiWarps + 3) * 32;
+constexpr int kThreadsTc = (kEpiWarps + 4) * 32;
 constexpr int kMmaWarp = 8;
 constexpr int kProdWarp = 9;
-constexpr int kPlanWarp = 10;
-constexpr int kPlanQ = 256;       // planned tiles the planner may run ahead of the producer
+constexpr int kPlanWarp = 10;     // planners: warps 10 and 11
+constexpr int kPlanners = 2;
+constexpr int kPlanQ = 256;       // planned tiles: two queues of kPlanQh, one per planner
+constexpr int kPlanQh = kPlanQ / kPlanners;
 constexpr int kBN = 128;          // columns per B tile
 constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere per block)
 constexpr int kMaxStages = 8;
@@ -140,11 +144,27 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+// The MMAs of one tile: KS steps of K = 16 into the two row halves' accumulators
+// (columns d0 and d0 + kBN), each chain starting with accumulate = 0.  KS is a template
+// argument so that the issuing thread runs straight-line code (a runtime bound on an
+// unrolled loop cost about sixty cycles per step slot, issued or not).
+template <int KS>
+__device__ __forceinline__ void mma_tile(uint32_t d0, uint64_t a0, uint64_t a1, uint64_t b0, uint32_t idesc);
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
                  : "memory");
+}
+
+template <int KS>
+__device__ __forceinline__ void mma_tile(uint32_t d0, uint64_t a0, uint64_t a1, uint64_t b0, uint32_t idesc)
+{
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) mma_f16(d0, a0 + 16u * kk, b0 + 16u * kk, idesc, kk > 0 ? 1u : 0u);
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) mma_f16(d0 + kBN, a1 + 16u * kk, b0 + 16u * kk, idesc, kk > 0 ? 1u : 0u);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
@@ -210,10 +230,10 @@ struct __align__(8) TcShared {
     int nvalid[2];
     unsigned int warps_in[2];    // epilogue warps holding rows of each part (bit masks)
     int npub;                    // epilogue warps that have published a threshold
-    int plan_ct[kPlanQ];         // planned column tiles (-1: end), a ring of kPlanQ ...
+    int plan_ct[kPlanQ];         // planned column tiles (-1: end), a ring of kPlanQh per planner ...
     unsigned int plan_mask[kPlanQ];   // ... with the epilogue warps that need them
     uint32_t plan_comp[kPlanQ];       // ... and, in masked sweeps, the tile's component
-    int plan_head, plan_tail;
+    int plan_head[kPlanners], plan_tail[kPlanners];
     unsigned int lup_bits[2];    // largest landmark distance bound of each row part    // entries written by the planner / taken by the producer
     unsigned int cmin, cmax;     // smallest and largest component among the tile's rows
 };
@@ -297,8 +317,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         sh->nvalid[0] = sh->nvalid[1] = 0;
         sh->warps_in[0] = sh->warps_in[1] = 0u;
         sh->npub = 0;
-        sh->plan_head = 0;
-        sh->plan_tail = 0;
+        for (int p = 0; p < kPlanners; ++p) sh->plan_head[p] = sh->plan_tail[p] = 0;
         sh->cmin = 0xFFFFFFFFu;
         sh->cmax = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -387,37 +406,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     const uint64_t wait_ns = a.wait_ns;
 
     if (warp == kProdWarp) {
-        // Producer: takes the planned tiles in order and stages each into the B ring with
-        // the epilogue warps that need it; -1 ends the sequence (and travels with the
-        // stages as the end marker).
+        // Producer: takes the planned tiles from the planners' queues (whichever has one,
+        // alternating when both do) and stages each into the B ring with the epilogue warps
+        // that need it.  A planner ends its queue with -1; when every queue has ended, -1
+        // travels with the stages as the end marker.
         int issued = 0;
-        for (int taken = 0;; ++taken) {
-            // wait for the planner (bounded; the whole warp polls)
-            const uint64_t t0 = global_ns();
-            bool ok = true;
-            while (((volatile int *)&sh->plan_head)[0] <= taken) {
-                if (*abort_flag || global_ns() - t0 > wait_ns) {
-                    ok = false;
-                    break;
-                }
-                __nanosleep(32);
-            }
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                *abort_flag = 1;
-                break;
-            }
-            __threadfence_block();
-            const int ct = ((volatile int *)sh->plan_ct)[taken % kPlanQ];
-            const unsigned int wmask = ((volatile unsigned int *)sh->plan_mask)[taken % kPlanQ];
-            const uint32_t tcomp = ((volatile uint32_t *)sh->plan_comp)[taken % kPlanQ];
-            __syncwarp();
-            if (lane == 0) ((volatile int *)&sh->plan_tail)[0] = taken + 1;
+        int taken0 = 0, taken1 = 0;     // entries taken from each queue
+        bool end0 = false, end1 = false;
+        int last = 1;
+        // stage one tile (or the end marker, ct < 0) into the ring
+        auto stage = [&](int ct, unsigned int wmask, uint32_t tcomp) -> bool {
             const int s = issued % kStages;
-            if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag, wait_ns)) {
-                *abort_flag = 1;
-                break;
-            }
+            if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag, wait_ns))
+                return false;
             if (lane == 0) {
                 sh->ring_tile[s] = ct;
                 sh->ring_mask[s] = wmask;
@@ -431,8 +432,51 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             ++issued;
             __syncwarp();
-            if (ct < 0) break;
+            return true;
+        };
+        bool ok = true;
+        for (;;) {
+            // wait for an entry in some queue, or for the end of all of them (bounded; the
+            // whole warp polls and takes lane 0's reading, so that it decides as one)
+            const uint64_t t0 = global_ns();
+            int q = -1;
+            for (uint32_t it = 0;; ++it) {
+                const int h0 = __shfl_sync(0xffffffffu, ((volatile int *)sh->plan_head)[0], 0);
+                const int h1 = __shfl_sync(0xffffffffu, ((volatile int *)sh->plan_head)[1], 0);
+                const bool r0 = !end0 && h0 > taken0, r1 = !end1 && h1 > taken1;
+                if (r0 || r1) {
+                    q = (r0 && r1) ? (last ^ 1) : (r0 ? 0 : 1);
+                    break;
+                }
+                if (end0 && end1) break;
+                if (__shfl_sync(0xffffffffu, (int)(*abort_flag != 0 || global_ns() - t0 > wait_ns), 0)) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            if (!ok || q < 0) break;
+            __threadfence_block();
+            const int n = q == 0 ? taken0 : taken1;
+            const int at = q * kPlanQh + n % kPlanQh;
+            const int ct = ((volatile int *)sh->plan_ct)[at];
+            const unsigned int wmask = ((volatile unsigned int *)sh->plan_mask)[at];
+            const uint32_t tcomp = ((volatile uint32_t *)sh->plan_comp)[at];
+            __syncwarp();
+            if (lane == 0) ((volatile int *)sh->plan_tail)[q] = n + 1;
+            if (q == 0) {
+                ++taken0;
+                end0 = ct < 0;
+            } else {
+                ++taken1;
+                end1 = ct < 0;
+            }
+            last = q;
+            if (ct < 0) continue;
+            if (!(ok = stage(ct, wmask, tcomp))) break;
         }
+        if (ok) ok = stage(-1, 0u, kInvalid);
+        if (!ok) *abort_flag = 1;
         // drain: every issued copy must have landed before the CTA exits
         if (lane == 0) {
             for (int q = issued - kStages < 0 ? 0 : issued - kStages; q < issued; ++q) {
@@ -442,12 +486,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
         }
         __syncwarp();
-    } else if (warp == kPlanWarp) {
-        // Planner: decides which column tiles to take, ahead of the producer (at most
-        // kPlanQ tiles), so that the bound computations overlap the copies and the MMAs.
-        // A tile is skipped when the lower bound of its candidate values exceeds the
-        // threshold of every row that could use it (the epilogue's published maxima,
-        // possibly stale = larger = safe).
+    } else if (warp == kPlanWarp || warp == kPlanWarp + 1) {
+        // Planners: decide which column tiles to take, ahead of the producer (at most
+        // kPlanQh tiles each), so that the bound computations overlap the copies and the
+        // MMAs.  Planner p takes the column blocks at odd or even places of the cyclic
+        // order (a fixed split: every block is decided by exactly one planner).  A tile is
+        // skipped when the lower bound of its candidate values exceeds the threshold of
+        // every row that could use it (the epilogue's published maxima, possibly stale =
+        // larger = safe).
+        const int pl = warp - kPlanWarp;
         float rhoR[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
@@ -456,11 +503,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         const unsigned int win0 = sh->warps_in[0], win1 = sh->warps_in[1];
         int planned = 0;
         bool ok_all = true;
-        // append (ct, wmask) to the plan (bounded wait for room; the whole warp polls)
-        auto push = [&](int ct, unsigned int wmask, uint32_t tcomp) -> bool {
+        volatile int *q_ct = (volatile int *)sh->plan_ct + pl * kPlanQh;
+        volatile unsigned int *q_mask = (volatile unsigned int *)sh->plan_mask + pl * kPlanQh;
+        volatile uint32_t *q_comp = (volatile uint32_t *)sh->plan_comp + pl * kPlanQh;
+        // bounded wait (the whole warp polls) for room for n more entries in this queue
+        auto room = [&](int n) -> bool {
             const uint64_t t0 = global_ns();
             bool ok = true;
-            while (planned - ((volatile int *)&sh->plan_tail)[0] >= kPlanQ) {
+            while (planned + n - ((volatile int *)sh->plan_tail)[pl] > kPlanQh) {
                 if (*abort_flag || global_ns() - t0 > wait_ns) {
                     ok = false;
                     break;
@@ -468,18 +518,42 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 __nanosleep(32);
             }
             ok = __all_sync(0xffffffffu, ok);
-            if (!ok) {
-                *abort_flag = 1;
-                return false;
-            }
+            if (!ok) *abort_flag = 1;
+            return ok;
+        };
+        // append one entry (ct, wmask, tcomp), written by lane 0
+        auto push = [&](int ct, unsigned int wmask, uint32_t tcomp) -> bool {
+            if (!room(1)) return false;
             if (lane == 0) {
-                ((volatile int *)sh->plan_ct)[planned % kPlanQ] = ct;
-                ((volatile unsigned int *)sh->plan_mask)[planned % kPlanQ] = wmask;
-                ((volatile uint32_t *)sh->plan_comp)[planned % kPlanQ] = tcomp;
+                q_ct[planned % kPlanQh] = ct;
+                q_mask[planned % kPlanQh] = wmask;
+                q_comp[planned % kPlanQh] = tcomp;
                 __threadfence_block();
-                ((volatile int *)&sh->plan_head)[0] = planned + 1;
+                ((volatile int *)sh->plan_head)[pl] = planned + 1;
             }
             ++planned;
+            __syncwarp();
+            return true;
+        };
+        // append the entries of the lanes with keep, in lane order, with one update of the head
+        auto push_step = [&](bool keep, int ct, unsigned int wmask, uint32_t tcomp) -> bool {
+            const unsigned int km = __ballot_sync(0xffffffffu, keep);
+            if (!km) return true;
+            const int nk = __popc(km);
+            if (!room(nk)) return false;
+            if (keep) {
+                const int at = (planned + __popc(km & ((1u << lane) - 1u))) % kPlanQh;
+                q_ct[at] = ct;
+                q_mask[at] = wmask;
+                q_comp[at] = tcomp;
+                __threadfence_block();
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                ((volatile int *)sh->plan_head)[pl] = planned + nk;
+            }
+            planned += nk;
             __syncwarp();
             return true;
         };
@@ -525,7 +599,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             // The wait is bounded; on time-out the decisions only get less selective.
             if (!(COLLECT || a.row_B) && nblk > 0) {
                 first = split == 0 ? tile0 : (blk_at(0) * kBlkTiles > rtb ? blk_at(0) * kBlkTiles : rtb);
-                ok_all = push(first, 0xFFu, a.comp ? a.tile_comp[first] : kInvalid);
+                if (pl == 0) ok_all = push(first, 0xFFu, a.comp ? a.tile_comp[first] : kInvalid);
             }
             if (ok_all && nblk > 0 && lane == 0) {
                 const uint64_t t0 = global_ns();
@@ -534,14 +608,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             }
             __syncwarp();
         }
-        // Level 1: 32 blocks per step, one per lane, against the blocks' spheres.  Level 2:
-        // in each block some warp needs, its tiles (one per lane) against the tiles' two
-        // spheres; the tile is skipped when no warp needs it.
+        // Level 1: 32 blocks per step, one per lane (this planner's half of them), against
+        // the blocks' spheres.  Level 2: in each block some warp needs, its tiles (one per
+        // lane) against the tiles' two spheres; the tile is skipped when no warp needs it.
         for (int u0 = 0; ok_all && u0 < nblk; u0 += 32) {
             const int nb = nblk - u0 < 32 ? nblk - u0 : 32;
-            bool bneed = lane < nb;
+            bool bneed = lane < nb && (lane & 1) == pl;
             range_tiles += __reduce_add_sync(0xffffffffu, lane < nb ? blk_tiles(blk_at(u0 + lane)) : 0);
-            if (lane < nb && a.prune) {
+            if (bneed && a.prune) {
                 const int cb = blk_at(u0 + lane);
                 float lb0, lb1;
                 part_bounds(a.blk_c + (int64_t)cb * a.d, a.blk_rho[cb], lb0, lb1);
@@ -574,20 +648,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                         wmask = need_mask(lb0, lb1);
                     }
                 }
-                unsigned int keepm = __ballot_sync(0xffffffffu, wmask != 0u);
-                while (keepm) {
-                    const int e = __ffs(keepm) - 1;
-                    keepm &= keepm - 1u;
-                    const unsigned int m = __shfl_sync(0xffffffffu, wmask, e);
-                    const uint32_t tc = __shfl_sync(0xffffffffu, tcomp, e);
-                    if (!(ok_all = push(t0c + e, m, tc))) break;
-                }
+                ok_all = push_step(wmask != 0u, t0c + lane, wmask, tcomp);
             }
         }
         if (ok_all) push(-1, 0u, kInvalid);
         const int taken = planned > 0 ? planned - 1 : 0;   // tiles, without the end marker
         if (lane == 0 && a.st_tiles) {
-            atomicAdd(&a.st_tiles[0], (unsigned long long)(range_tiles - taken));
+            // skipped = the range's tiles (counted once) less the tiles either planner took
+            atomicAdd(&a.st_tiles[0], (unsigned long long)((pl == 0 ? (long long)range_tiles : 0ll) - taken));
             atomicAdd(&a.st_tiles[1], (unsigned long long)taken);
         }
     } else if (warp == kMmaWarp) {
@@ -621,13 +689,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                     // stage's base plus 16 per K step of 16 (256 bytes); shared addresses stay
                     // below 2^18, so the field never carries into the next one
                     const uint64_t bd0 = bdesc0 + (uint64_t)(((uint32_t)s * b_bytes) >> 4);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t d_tmem = tmem + (uint32_t)((b * 2 + h) * kBN);
-                        const uint64_t ad0 = adesc0[h];
-#pragma unroll
-                        for (int kk = 0; kk < kMaxKSteps; ++kk)
-                            if (kk < ksteps) mma_f16(d_tmem, ad0 + 16u * kk, bd0 + 16u * kk, idesc, kk > 0 ? 1u : 0u);
+                    const uint32_t d0 = tmem + (uint32_t)(b * 2 * kBN);
+                    switch (ksteps) {
+                    case 1: mma_tile<1>(d0, adesc0[0], adesc0[1], bd0, idesc); break;
+                    case 2: mma_tile<2>(d0, adesc0[0], adesc0[1], bd0, idesc); break;
+                    case 3: mma_tile<3>(d0, adesc0[0], adesc0[1], bd0, idesc); break;
+                    case 4: mma_tile<4>(d0, adesc0[0], adesc0[1], bd0, idesc); break;
+                    case 5: mma_tile<5>(d0, adesc0[0], adesc0[1], bd0, idesc); break;
+                    default: mma_tile<6>(d0, adesc0[0], adesc0[1], bd0, idesc); break;
                     }
                     mma_commit(&sh->empty[s]);
                     mma_commit(&sh->tfull[b]);
