@@ -38,7 +38,7 @@ constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere
 constexpr int kMaxStages = 8;
 constexpr int kMaxKSteps = 6;     // K steps of 16 per tile: kpad <= 96 (split BF16 at d <= 30)
 constexpr int kBandWide = 64;   // band slots per row for one-term BF16 (a wide band)
-constexpr int kStageStride = 36;   // floats per thread in the hit-staging area (16-byte rows, no bank conflicts)
+constexpr int kInfoQ = kMaxStages + 2;   // tile records in flight: the ring's stages plus the two TMEM buffers
 // Waits for work (stages, accumulators, plan entries, thresholds) give up after the
 // caller's limit (SweepArgs::wait_ns, 2 s by default).  The drain waits at the end --
 // copies and MMAs this CTA issued, which must land before its shared memory and TMEM
@@ -195,6 +195,22 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32])
         : "memory");
 }
 
+// w[q] for a q known only at run time, without local memory: a five-level selection
+// by the bits of q (31 selects).
+__device__ __forceinline__ uint32_t pick32(const uint32_t (&w)[32], int q)
+{
+    uint32_t a[16], b[8], c[4], d[2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = (q & 1) ? w[2 * i + 1] : w[2 * i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = (q & 2) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = (q & 4) ? b[2 * i + 1] : b[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) d[i] = (q & 8) ? c[2 * i + 1] : c[2 * i];
+    return (q & 16) ? d[1] : d[0];
+}
+
 // Order-only barrier for 32 more registers after a wait (asm volatile keeps the order).
 __device__ __forceinline__ void reg_fence(uint32_t (&v)[32])
 {
@@ -217,12 +233,13 @@ struct __align__(8) TcShared {
     uint64_t drain;
     uint32_t tmem_base;
     int abort_flag;
-    int ring_tile[kMaxStages];   // column tile in each B stage (-1: end of the sequence)
-    int acc_tile[2];             // column tile in each TMEM buffer (-1: end)
-    unsigned int ring_mask[kMaxStages];   // epilogue warps that need the tile in each stage
-    unsigned int acc_mask[2];             // ... and in each TMEM buffer
-    uint32_t ring_comp[kMaxStages];       // masked sweeps: the tile's component (kInvalid: mixed)
-    uint32_t acc_comp[2];
+    // Record of the q-th staged tile at q % kInfoQ, written by the producer and read by
+    // the MMA warp and the epilogue: the producer is at most kStages tiles ahead of the
+    // MMAs and those at most two ahead of the epilogue, so a record is read before it is
+    // written again.
+    int info_tile[kInfoQ];              // column tile (-1: end of the sequence)
+    unsigned int info_mask[kInfoQ];     // epilogue warps that need the tile
+    uint32_t info_comp[kInfoQ];         // masked sweeps: the tile's component (kInvalid: mixed)
     float warp_thr[kEpiWarps];   // largest row threshold of each epilogue warp
     float cR[2][32];             // row tile spheres (part 0: the first landmark group of the
     unsigned int rho_bits[2];    // tile's rows, part 1: the rest): centres, radii,
@@ -244,7 +261,7 @@ static_assert(sizeof(TcShared) <= kShBytes, "shared control block");
 __host__ __device__ inline int tc_stages(int kpad, int band)
 {
     const size_t fixed = (size_t)kRowTile * kpad * 2 + kShBytes + (size_t)band * kRowTile * 8 +
-                         (size_t)kRowTile * kStageStride * 4 + 1024;
+                         1024;
     const size_t per = (size_t)kBN * kpad * 2;
     int s = (int)((225 * 1024 - fixed) / per);
     return s > kMaxStages ? kMaxStages : s;
@@ -263,7 +280,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
     TcShared *sh = reinterpret_cast<TcShared *>(sB + (size_t)kStages * b_bytes);
     float *band_v = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(sh) + kShBytes);   // [CB][256]
     uint32_t *band_j = reinterpret_cast<uint32_t *>(band_v + CB * kRowTile);
-    float *stage_v = reinterpret_cast<float *>(band_j + CB * kRowTile);                  // [256][kStageStride]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int split = blockIdx.y;
@@ -420,9 +436,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag, wait_ns))
                 return false;
             if (lane == 0) {
-                sh->ring_tile[s] = ct;
-                sh->ring_mask[s] = wmask;
-                sh->ring_comp[s] = tcomp;
+                ((volatile int *)sh->info_tile)[issued % kInfoQ] = ct;
+                ((volatile unsigned int *)sh->info_mask)[issued % kInfoQ] = wmask;
+                ((volatile uint32_t *)sh->info_comp)[issued % kInfoQ] = tcomp;
                 if (ct < 0) {
                     mbar_arrive(&sh->full[s]);
                 } else {
@@ -677,13 +693,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             // lane 0 observed the stage (acquire); it reads the tile number and the warp
             // takes its decision from lane 0 so that all lanes stay together
             int tile = 0;
-            if (lane == 0) tile = ((volatile int *)sh->ring_tile)[s];
+            if (lane == 0) tile = ((volatile int *)sh->info_tile)[q % kInfoQ];
             tile = __shfl_sync(0xffffffffu, tile, 0);
             tc_fence_after();
             if (lane == 0) {
-                ((volatile int *)sh->acc_tile)[b] = tile;
-                ((volatile unsigned int *)sh->acc_mask)[b] = ((volatile unsigned int *)sh->ring_mask)[s];
-                ((volatile uint32_t *)sh->acc_comp)[b] = ((volatile uint32_t *)sh->ring_comp)[s];
                 if (tile >= 0) {
                     // descriptors: the start-address field (bits 0-13, address >> 4) of the
                     // stage's base plus 16 per K step of 16 (256 bytes); shared addresses stay
@@ -703,7 +716,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 } else {
                     mbar_arrive(&sh->tfull[b]);   // no MMA for the end marker
                 }
-                mbar_arrive(&sh->tfull[b]);       // publishes acc_tile[b]
+                mbar_arrive(&sh->tfull[b]);       // passes the producer's tile record on (release)
             }
             __syncwarp();
             if (tile < 0) break;
@@ -726,7 +739,6 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         const RowConst rc = valid ? make_rowconst(a.sc, a.m, a.pos2row[myrow]) : RowConst{0.f, 0.f};
         float *bv = band_v + threadIdx.x;
         uint32_t *bj = band_j + threadIdx.x;
-        float *stg = stage_v + threadIdx.x * kStageStride;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
         // A bounded row starts at the threshold of its bound; thresholds already published
         // for these rows by other column ranges apply too.  Then the warp's first
@@ -763,7 +775,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             const int l2c = __vimin3_s32(l1[6], l1[7], l1[8]), l2d = min(l1[9], l1[10]);
             return min(__vimin3_s32(l2a, l2b, l2c), l2d);
         };
-        // The exact walk of one 32-column chunk through this thread's shared-memory row.
+        // The exact walk of one 32-column chunk: the columns whose value passes the
+        // threshold, in order, each value taken from the registers by its column number.
         uint32_t tcomp = kInvalid;   // component of the current column tile (kInvalid: mixed)
         // the columns of this row's instance (all columns when not batched)
         int64_t ibeg = 0, iend = a.N;
@@ -775,15 +788,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             const float thr = COLLECT ? cthr : sel.thr;
             uint32_t mask = 0;
 #pragma unroll
-            for (int q = 0; q < 32; q += 4)
-                *reinterpret_cast<float4 *>(stg + q) = make_float4(__uint_as_float(w[q]), __uint_as_float(w[q + 1]),
-                                                                   __uint_as_float(w[q + 2]), __uint_as_float(w[q + 3]));
-#pragma unroll
             for (int q = 0; q < 32; ++q) mask |= (__uint_as_float(w[q]) <= thr ? 1u : 0u) << q;
             while (mask) {
                 const int q = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const float val = stg[q];
+                const float val = __uint_as_float(pick32(w, q));
                 const int64_t j = jbase + q;
                 if (!(val <= (COLLECT ? cthr : sel.thr))) continue;
                 if (j >= a.N || (uint32_t)j == myrow) continue;
@@ -810,10 +819,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             int tw = 0;
             uint32_t tcm = kInvalid;
             if (lane == 0) {
-                const int tl = ((volatile int *)sh->acc_tile)[b];
-                const unsigned int m = ((volatile unsigned int *)sh->acc_mask)[b];
+                const int tl = ((volatile int *)sh->info_tile)[q % kInfoQ];
+                const unsigned int m = ((volatile unsigned int *)sh->info_mask)[q % kInfoQ];
                 tw = tl < 0 ? -1 : (tl << 1) | (int)((m >> warp) & 1u);
-                tcm = ((volatile uint32_t *)sh->acc_comp)[b];
+                tcm = ((volatile uint32_t *)sh->info_comp)[q % kInfoQ];
             }
             tw = __shfl_sync(0xffffffffu, tw, 0);
             if (tw < 0) break;
@@ -884,7 +893,7 @@ size_t sweep_tc_smem_bytes(int kpad, int band)
 {
     // at least ~half of the SM's shared memory keeps one CTA per SM (it holds all of TMEM)
     const size_t need = (size_t)kRowTile * kpad * 2 + (size_t)tc_stages(kpad, band) * kBN * kpad * 2 + kShBytes +
-                        (size_t)band * kRowTile * 8 + (size_t)kRowTile * kStageStride * 4 + 1024;
+                        (size_t)band * kRowTile * 8 + 1024;
     const size_t one_per_sm = 120 * 1024;
     return need > one_per_sm ? need : one_per_sm;
 }
