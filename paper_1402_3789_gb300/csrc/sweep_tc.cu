@@ -31,7 +31,7 @@ constexpr int kMmaWarp = 8;
 constexpr int kProdWarp = 9;
 constexpr int kPlanWarp = 10;     // planners: warps 10 and 11
 constexpr int kPlanners = 2;
-constexpr int kPlanQ = 256;       // planned tiles: two queues of kPlanQh, one per planner
+constexpr int kPlanQ = 1024;      // planned tiles: two queues of kPlanQh, one per planner
 constexpr int kPlanQh = kPlanQ / kPlanners;
 constexpr int kBN = 128;          // columns per B tile
 constexpr int kBlkTiles = 32;     // tiles per column block (one bounding sphere per block)
@@ -254,7 +254,7 @@ struct __align__(8) TcShared {
     unsigned int lup_bits[2];    // largest landmark distance bound of each row part    // entries written by the planner / taken by the producer
     unsigned int cmin, cmax;     // smallest and largest component among the tile's rows
 };
-constexpr int kShBytes = 4096;
+constexpr int kShBytes = 16384;
 static_assert(sizeof(TcShared) <= kShBytes, "shared control block");
 
 // Shared-memory stages of the B ring that fit next to the other regions.
