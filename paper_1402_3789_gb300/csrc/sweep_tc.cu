@@ -682,19 +682,20 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         const uint64_t adesc0[2] = {smem_desc(aaddr, lbo, sbo), smem_desc(aaddr + 16u * sbo, lbo, sbo)};
         const uint64_t bdesc0 = smem_desc(baddr, lbo, sbo);
         int done = 0;
+        // stage, its phase and the record slot of tile q, kept as counters (kStages is a
+        // run-time value, and a division per tile is not free on this path)
+        int s = 0, qi = 0;
+        uint32_t sph = 0;
         for (int q = 0;; ++q) {
-            const int s = q % kStages, b = q & 1;
-            bool ok = mbar_wait_warp(&sh->full[s], (q / kStages) & 1, abort_flag, wait_ns);
+            const int b = q & 1;
+            bool ok = mbar_wait_warp(&sh->full[s], sph, abort_flag, wait_ns);
             if (ok && q >= 2) ok = mbar_wait_warp(&sh->tempty[b], ((q >> 1) - 1) & 1, abort_flag, wait_ns);
             if (!ok) {
                 *abort_flag = 1;
                 break;
             }
-            // lane 0 observed the stage (acquire); it reads the tile number and the warp
-            // takes its decision from lane 0 so that all lanes stay together
-            int tile = 0;
-            if (lane == 0) tile = ((volatile int *)sh->info_tile)[q % kInfoQ];
-            tile = __shfl_sync(0xffffffffu, tile, 0);
+            // every lane observed the stage (acquire) and reads the same record word
+            const int tile = ((volatile int *)sh->info_tile)[qi];
             tc_fence_after();
             if (lane == 0) {
                 if (tile >= 0) {
@@ -721,6 +722,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
             __syncwarp();
             if (tile < 0) break;
             done = q + 1;
+            if (++s == kStages) {
+                s = 0;
+                sph ^= 1u;
+            }
+            if (++qi == kInfoQ) qi = 0;
         }
         // every issued MMA completes before TMEM is freed
         if (lane == 0 && done > 0) {
