@@ -431,14 +431,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
         bool end0 = false, end1 = false;
         int last = 1;
         // stage one tile (or the end marker, ct < 0) into the ring
+        int s = 0, qi = 0;       // ring stage and record slot of the next staged tile
+        uint32_t eph = 1u;       // parity of the stage's empty phase to wait for
         auto stage = [&](int ct, unsigned int wmask, uint32_t tcomp) -> bool {
-            const int s = issued % kStages;
-            if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], ((issued / kStages) - 1) & 1, abort_flag, wait_ns))
-                return false;
+            if (issued >= kStages && !mbar_wait_warp(&sh->empty[s], eph, abort_flag, wait_ns)) return false;
             if (lane == 0) {
-                ((volatile int *)sh->info_tile)[issued % kInfoQ] = ct;
-                ((volatile unsigned int *)sh->info_mask)[issued % kInfoQ] = wmask;
-                ((volatile uint32_t *)sh->info_comp)[issued % kInfoQ] = tcomp;
+                ((volatile int *)sh->info_tile)[qi] = ct;
+                ((volatile unsigned int *)sh->info_mask)[qi] = wmask;
+                ((volatile uint32_t *)sh->info_comp)[qi] = tcomp;
                 if (ct < 0) {
                     mbar_arrive(&sh->full[s]);
                 } else {
@@ -447,6 +447,11 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_sweep_tc(const SweepArgs a)
                 }
             }
             ++issued;
+            if (++s == kStages) {
+                s = 0;
+                eph ^= 1u;
+            }
+            if (++qi == kInfoQ) qi = 0;
             __syncwarp();
             return true;
         };
