@@ -123,12 +123,13 @@ cudaError_t launch_landmark_chain(const float *X, int64_t N, int d, int64_t L, u
 // order with one FMA each; DP = d rounded up to 4 (the padding adds 0 * 0, which changes
 // no sum).  Each thread takes two queries, so every float4 of a reference row read from
 // shared memory feeds eight FMAs.
-template <int DP>
+template <int DP, int DC = DP>   // DP: padded width (float4 loads), DC: features summed (DC <= DP)
 __global__ void __launch_bounds__(256) k_nearest_ref(const float *__restrict__ X, int64_t N, int d, int64_t Q,
                                                      int64_t R, uint32_t *__restrict__ arg_out,
                                                      float *__restrict__ dist_out)
 {
     __shared__ __align__(16) float lm[kLandChunk * DP];
+    __shared__ int64_t lrow[kLandChunk];   // the chunk's landmark rows
     const int64_t qa = (int64_t)blockIdx.x * 512 + threadIdx.x, qb = qa + 256;
     const int64_t ra = qa < Q ? qa * N / Q : 0, rb = qb < Q ? qb * N / Q : 0;
     float xa[DP], xb[DP];
@@ -141,10 +142,12 @@ __global__ void __launch_bounds__(256) k_nearest_ref(const float *__restrict__ X
     int64_t arga = 0, argb = 0;
     for (int64_t m0 = 0; m0 < R; m0 += kLandChunk) {
         __syncthreads();
+        if (threadIdx.x < kLandChunk) lrow[threadIdx.x] = (m0 + threadIdx.x) * N / R;   // one division per landmark
+        __syncthreads();
         for (int t = threadIdx.x; t < kLandChunk * DP; t += blockDim.x) {
             const int64_t m = m0 + t / DP;
             const int k = t % DP;
-            lm[t] = (m < R && k < d) ? X[(m * N / R) * d + k] : 0.0f;
+            lm[t] = (m < R && k < d) ? X[lrow[t / DP] * d + k] : 0.0f;
         }
         __syncthreads();
         const int cnt = (int)(R - m0 < kLandChunk ? R - m0 : kLandChunk);
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(256) k_nearest_ref(const float *__restrict__ X
                 const float l[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    if (4 * k4 + j >= DC) continue;   // zero padding: would add +0 exactly
                     const float ea = xa[4 * k4 + j] - l[j], eb = xb[4 * k4 + j] - l[j];
                     acca = fmaf(ea, ea, acca);
                     accb = fmaf(eb, eb, accb);
@@ -193,7 +197,10 @@ cudaError_t launch_nearest_ref(const float *X, int64_t N, int d, int64_t Q, int6
     case 4: k_nearest_ref<16><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
     case 5: k_nearest_ref<20><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
     case 6: k_nearest_ref<24><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
-    case 7: k_nearest_ref<28><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
+    case 7:
+        if (d == 25) k_nearest_ref<28, 25><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist);   // the paper's width
+        else k_nearest_ref<28><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist);
+        break;
     default: k_nearest_ref<32><<<blocks, 256, 0, s>>>(X, N, d, Q, R, arg, dist); break;
     }
     count_launches(1);

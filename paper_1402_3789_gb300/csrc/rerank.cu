@@ -180,10 +180,21 @@ __device__ int exact_distances(const float *xi, const float *X, int d, double *w
             wD[e] = INFINITY;
         }
         __syncwarp();
+        // (candidate c, feature f) of the lane's pairs q = lane, lane + 32, ...: stepped
+        // rather than divided (d is a run-time value)
+        int c = 0, f = lane;
+        while (f >= d) {
+            f -= d;
+            ++c;
+        }
         for (int q = lane; q < nb * d; q += 32) {
-            const int c = q / d, f = q - c * d;
             const double ev = __dsub_rn((double)xi[f], (double)X[(int64_t)cj[c] * d + f]);
             tsm[c * stride + f] = metric == 0 ? __dmul_rn(ev, ev) : fabs(ev);
+            f += 32;
+            while (f >= d) {
+                f -= d;
+                ++c;
+            }
         }
         __syncwarp();
         if (lane < nb) {
