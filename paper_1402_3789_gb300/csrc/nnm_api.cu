@@ -19,6 +19,7 @@
 #include <string>
 #include <utility>
 #include <vector>
+#include <mutex>
 
 #include "nnm_internal.cuh"
 
@@ -162,27 +163,67 @@ nnm_status fail(nnm_ctx *c, nnm_status s, const char *fmt, ...)
         if (s_ != NNM_OK) return s_;               \
     } while (0)
 
+// Device memory of the library comes from a memory pool of its own, allocated and freed
+// in stream order on the context's stream: after the first context, creating and
+// destroying contexts costs no cudaMalloc / cudaFree (the pool keeps what it has grown
+// to), and the process's default pool is left as the user set it.
+cudaMemPool_t lib_pool()
+{
+    static std::mutex m;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> g(m);
+    if (!pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        if (cudaMemPoolCreate(&pools[dev], &props) != cudaSuccess) {
+            cudaGetLastError();
+            pools[dev] = nullptr;
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    return pools[dev];
+}
+
+// count elements of T in stream order on s (the library's pool; the default pool if it
+// could not be created)
+template <typename T>
+cudaError_t pool_alloc(T **p, size_t count, cudaStream_t s)
+{
+    cudaMemPool_t pool = lib_pool();
+    const size_t bytes = (count ? count : 1) * sizeof(T);
+    return pool ? cudaMallocFromPoolAsync((void **)p, bytes, pool, s) : cudaMallocAsync((void **)p, bytes, s);
+}
+
 template <typename T>
 nnm_status dalloc(nnm_ctx *c, T **p, size_t count)
 {
     if (*p) {
-        cudaFree(*p);
+        cudaFreeAsync(*p, c->stream);
         *p = nullptr;
     }
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    cudaError_t e = pool_alloc(p, count, c->stream);
     if (e != cudaSuccess) {
         *p = nullptr;
         cudaGetLastError();
-        return fail(c, NNM_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return fail(c, NNM_ENOMEM, "allocation of %zu bytes failed: %s", (count ? count : 1) * sizeof(T),
+                    cudaGetErrorString(e));
     }
     return NNM_OK;
 }
 
 template <typename T>
-void dfree(T *&p)
+void dfree(nnm_ctx *c, T *&p)
 {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, c->stream);
     p = nullptr;
 }
 
@@ -677,18 +718,18 @@ nnm_status prepare(nnm_ctx *c)
         float *ldist = nullptr, *rdist = nullptr, *tau = nullptr;
         unsigned int *hist = nullptr;
         auto free_all = [&]() {
-            cudaFree(keys);
-            cudaFree(tmp);
-            cudaFree(lkeys);
-            cudaFree(ltmp);
-            cudaFree(crank);
-            cudaFree(larg);
-            cudaFree(lpos);
-            cudaFree(lrank);
-            cudaFree(rarg);
-            cudaFree(ldist);
-            cudaFree(tau);
-            cudaFree(hist);
+            if (keys) cudaFreeAsync(keys, s);
+            if (tmp) cudaFreeAsync(tmp, s);
+            if (lkeys) cudaFreeAsync(lkeys, s);
+            if (ltmp) cudaFreeAsync(ltmp, s);
+            if (crank) cudaFreeAsync(crank, s);
+            if (larg) cudaFreeAsync(larg, s);
+            if (lpos) cudaFreeAsync(lpos, s);
+            if (lrank) cudaFreeAsync(lrank, s);
+            if (rarg) cudaFreeAsync(rarg, s);
+            if (ldist) cudaFreeAsync(ldist, s);
+            if (tau) cudaFreeAsync(tau, s);
+            if (hist) cudaFreeAsync(hist, s);
         };
         nnm_status st = NNM_OK;
         do {
@@ -775,8 +816,8 @@ nnm_status prepare(nnm_ctx *c)
         NNM_TRY(dalloc(c, &c->mu_f, (size_t)c->d));
         NNM_CUDA(c, cudaMemcpyAsync(c->mu_f, muf_h, c->d * sizeof(float), cudaMemcpyHostToDevice, s));
         NNM_CUDA(c, cudaStreamSynchronize(s));
-        cudaFree(partial);
-        cudaFree(mu);
+        cudaFreeAsync(partial, s);
+        cudaFreeAsync(mu, s);
         c->tile_w = 128;
         c->margin.tensor = 1;
         // FP32 accumulation of kpad exact products, order and rounding mode unknown:
@@ -1160,14 +1201,16 @@ nnm_status restrict_fast(nnm_ctx *c, const nnm_restrictions &r, double cap2, nnm
 
 constexpr int64_t kLiteralMaxRows = 262144;
 
-// Device buffers of one call, freed when it returns.
+// Device buffers of one call, freed (in stream order) when it returns.
 struct CallScratch {
+    explicit CallScratch(cudaStream_t st) : s(st) {}
+    cudaStream_t s;
     std::vector<void *> ptrs;
     template <typename T>
     cudaError_t get(T **p, size_t count)
     {
         *p = nullptr;
-        cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+        cudaError_t e = pool_alloc(p, count, s);
         if (e != cudaSuccess) {
             *p = nullptr;
             cudaGetLastError();
@@ -1180,14 +1223,14 @@ struct CallScratch {
     {
         for (auto &q : ptrs)
             if (q == p) {
-                cudaFree(q);
+                cudaFreeAsync(q, s);
                 q = nullptr;
             }
     }
     ~CallScratch()
     {
         for (void *p : ptrs)
-            if (p) cudaFree(p);
+            if (p) cudaFreeAsync(p, s);
     }
 };
 
@@ -1210,7 +1253,7 @@ nnm_status cluster_literal(nnm_ctx *c, const nnm_restrictions &r, double cap2, n
         return fail(c, NNM_EUNSUPPORTED, "the all-pairs reading (semantics 1) takes N <= %lld", (long long)kLiteralMaxRows);
     const int64_t N = c->N;
     cudaStream_t s = c->stream;
-    CallScratch sc;
+    CallScratch sc(c->stream);
     LitArgs a{};
     a.X = c->X;
     a.d = c->d;
@@ -1692,9 +1735,9 @@ nnm_status nnm_cluster_host(const float *X_host, int64_t N, int32_t d, nnm_metri
         return e == cudaErrorMemoryAllocation ? NNM_ENOMEM : NNM_ECUDA;
     };
     do {
-        cudaError_t e = cudaMalloc((void **)&X, (size_t)N * d * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&mg, (size_t)(N - 1) * sizeof(nnm_merge));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&lab, (size_t)N * sizeof(int32_t));
+        cudaError_t e = pool_alloc(&X, (size_t)N * d, s);
+        if (e == cudaSuccess) e = pool_alloc(&mg, (size_t)(N - 1), s);
+        if (e == cudaSuccess) e = pool_alloc(&lab, (size_t)N, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(X, X_host, (size_t)N * d * sizeof(float), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) {
             st = cuda_status(e);
@@ -1717,9 +1760,10 @@ nnm_status nnm_cluster_host(const float *X_host, int64_t N, int32_t d, nnm_metri
     } while (0);
     nnm_destroy(ctx);   // synchronises the stream before freeing
     if (!ctx) cudaStreamSynchronize(s);
-    cudaFree(X);
-    cudaFree(mg);
-    cudaFree(lab);
+    if (X) cudaFreeAsync(X, s);
+    if (mg) cudaFreeAsync(mg, s);
+    if (lab) cudaFreeAsync(lab, s);
+    cudaStreamSynchronize(s);
     return st;
 }
 
@@ -1749,97 +1793,97 @@ void nnm_destroy(nnm_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    dfree(c->pos2row);
-    dfree(c->tile_c);
-    dfree(c->tile_rho);
-    dfree(c->land_d2);
-    dfree(c->lup);
-    dfree(c->tile_lmin);
-    dfree(c->blk_lmin);
-    dfree(c->group);
-    dfree(c->inst_off);
-    dfree(c->inst_pos);
-    dfree(c->ebeg);
-    dfree(c->eend);
-    dfree(c->inst_nm);
-    dfree(c->inst_edges);
-    dfree(c->merges_tmp);
-    dfree(c->cut_cnt);
-    dfree(c->cut_lab);
-    dfree(c->cut_w);
-    dfree(c->cut_slot);
-    dfree(c->cut_hkey);
-    dfree(c->cut_hpar);
-    dfree(c->cut_hw);
-    dfree(c->cut_hsum);
-    dfree(c->cut_hlab);
-    dfree(c->fw_cand);
-    dfree(c->fw_walk);
-    dfree(c->fw_dec);
-    dfree(c->fw_unsafe);
-    dfree(c->fw_pos);
-    dfree(c->fw_blk);
-    dfree(c->fw_edges);
-    dfree(c->fw_cnt);
-    dfree(c->blk_c);
-    dfree(c->blk_rho);
-    dfree(c->mu_f);
-    dfree(c->row2pos);
-    dfree(c->list_pos);
-    dfree(c->Xs);
-    dfree(c->XA);
-    dfree(c->XB);
-    dfree(c->r);
-    dfree(c->P);
-    dfree(c->E);
-    dfree(c->cand_v);
-    dfree(c->cand_j);
-    dfree(c->cand_ovf);
-    dfree(c->ovf_row);
-    dfree(c->ovf_thr);
-    dfree(c->ovf_thr_slot);
-    dfree(c->ovf_flag);
-    dfree(c->ovf_blk);
-    dfree(c->slot_thr);
-    dfree(c->coll_cnt);
-    dfree(c->coll_j);
-    dfree(c->coll_D);
-    dfree(c->heavy_flag);
-    dfree(c->heavy_blk);
-    dfree(c->heavy_rows);
-    dfree(c->heavy_rows2);
-    dfree(c->heavy_thr);
-    dfree(c->heavy_thr2);
-    dfree(c->cache_j);
-    dfree(c->cache_D);
-    dfree(c->cache_n);
-    dfree(c->cache_exh);
-    dfree(c->row_B);
-    dfree(c->comp_bound);
-    dfree(c->comp_pos);
-    dfree(c->tile_comp);
-    dfree(c->comp);
-    dfree(c->parent);
-    dfree(c->list);
-    dfree(c->row_D);
-    dfree(c->row_ab);
-    dfree(c->best_D);
-    dfree(c->best_ab);
-    dfree(c->row_state);
-    dfree(c->frozen);
-    dfree(c->flag_pos);
-    dfree(c->block_cnt);
-    dfree(c->edges);
-    dfree(c->edges_tmp);
-    dfree(c->uf_parent);
-    dfree(c->uf_size);
-    dfree(c->deferred);
-    dfree(c->minm);
-    dfree(c->flag);
-    dfree(c->block_sums);
-    dfree(c->dcount);
-    dfree(c->dstat);
-    dfree(c->derr);
+    dfree(c, c->pos2row);
+    dfree(c, c->tile_c);
+    dfree(c, c->tile_rho);
+    dfree(c, c->land_d2);
+    dfree(c, c->lup);
+    dfree(c, c->tile_lmin);
+    dfree(c, c->blk_lmin);
+    dfree(c, c->group);
+    dfree(c, c->inst_off);
+    dfree(c, c->inst_pos);
+    dfree(c, c->ebeg);
+    dfree(c, c->eend);
+    dfree(c, c->inst_nm);
+    dfree(c, c->inst_edges);
+    dfree(c, c->merges_tmp);
+    dfree(c, c->cut_cnt);
+    dfree(c, c->cut_lab);
+    dfree(c, c->cut_w);
+    dfree(c, c->cut_slot);
+    dfree(c, c->cut_hkey);
+    dfree(c, c->cut_hpar);
+    dfree(c, c->cut_hw);
+    dfree(c, c->cut_hsum);
+    dfree(c, c->cut_hlab);
+    dfree(c, c->fw_cand);
+    dfree(c, c->fw_walk);
+    dfree(c, c->fw_dec);
+    dfree(c, c->fw_unsafe);
+    dfree(c, c->fw_pos);
+    dfree(c, c->fw_blk);
+    dfree(c, c->fw_edges);
+    dfree(c, c->fw_cnt);
+    dfree(c, c->blk_c);
+    dfree(c, c->blk_rho);
+    dfree(c, c->mu_f);
+    dfree(c, c->row2pos);
+    dfree(c, c->list_pos);
+    dfree(c, c->Xs);
+    dfree(c, c->XA);
+    dfree(c, c->XB);
+    dfree(c, c->r);
+    dfree(c, c->P);
+    dfree(c, c->E);
+    dfree(c, c->cand_v);
+    dfree(c, c->cand_j);
+    dfree(c, c->cand_ovf);
+    dfree(c, c->ovf_row);
+    dfree(c, c->ovf_thr);
+    dfree(c, c->ovf_thr_slot);
+    dfree(c, c->ovf_flag);
+    dfree(c, c->ovf_blk);
+    dfree(c, c->slot_thr);
+    dfree(c, c->coll_cnt);
+    dfree(c, c->coll_j);
+    dfree(c, c->coll_D);
+    dfree(c, c->heavy_flag);
+    dfree(c, c->heavy_blk);
+    dfree(c, c->heavy_rows);
+    dfree(c, c->heavy_rows2);
+    dfree(c, c->heavy_thr);
+    dfree(c, c->heavy_thr2);
+    dfree(c, c->cache_j);
+    dfree(c, c->cache_D);
+    dfree(c, c->cache_n);
+    dfree(c, c->cache_exh);
+    dfree(c, c->row_B);
+    dfree(c, c->comp_bound);
+    dfree(c, c->comp_pos);
+    dfree(c, c->tile_comp);
+    dfree(c, c->comp);
+    dfree(c, c->parent);
+    dfree(c, c->list);
+    dfree(c, c->row_D);
+    dfree(c, c->row_ab);
+    dfree(c, c->best_D);
+    dfree(c, c->best_ab);
+    dfree(c, c->row_state);
+    dfree(c, c->frozen);
+    dfree(c, c->flag_pos);
+    dfree(c, c->block_cnt);
+    dfree(c, c->edges);
+    dfree(c, c->edges_tmp);
+    dfree(c, c->uf_parent);
+    dfree(c, c->uf_size);
+    dfree(c, c->deferred);
+    dfree(c, c->minm);
+    dfree(c, c->flag);
+    dfree(c, c->block_sums);
+    dfree(c, c->dcount);
+    dfree(c, c->dstat);
+    dfree(c, c->derr);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
