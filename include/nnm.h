@@ -240,7 +240,7 @@ nnm_status nnm_cluster(nnm_ctx *ctx, const nnm_restrictions *restrictions, nnm_m
  *   merges_host     nnm_merge [N-1] host memory, written;  n_merges_host receives the count.
  *   labels_host     int32 [N] host memory, written;  n_clusters_host receives K.
  * The device memory the call needs (X, merges, labels and the context's workspace) is
- * allocated and freed inside the call.  N >= 2.  Errors: those of nnm_create and
+ * taken from the library's pool and given back inside the call (see nnm_destroy).  N >= 2.  Errors: those of nnm_create and
  * nnm_cluster. */
 nnm_status nnm_cluster_host(const float *X_host, int64_t N, int32_t d, nnm_metric metric,
                             nnm_precision precision, const nnm_options *options,
@@ -266,7 +266,11 @@ const char *nnm_last_error(const nnm_ctx *ctx);
 /* nnm_status_string -- static name of a status code. */
 const char *nnm_status_string(nnm_status s);
 
-/* nnm_destroy -- free the context and its device workspace.  NULL is ignored. */
+/* nnm_destroy -- free the context and its device workspace.  NULL is ignored.
+ * Device workspace (of contexts, of calls and of nnm_cluster_host) comes from a memory
+ * pool of the library, one per device, allocated and freed in stream order on the
+ * context's stream; freed workspace goes back to that pool, which keeps the memory it
+ * has grown to for the life of the process (the default pool is not touched). */
 void nnm_destroy(nnm_ctx *ctx);
 
 /* Largest N accepted by nnm_restrict_static. */
